@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark: A-Bruijn graph build throughput (edges inserted per second) on GB300.
+
+One step = one complete graph build of the workload into a pre-allocated
+table: K2 (empty the table) then K1 (insert every k-mer of every read), with
+the reads already resident in HBM.  ``value`` is edges/s over K timed steps
+(whole job, max over ranks; N > 1 runs independent replicas).  ``e2e`` is
+the same build through the host-buffer entry point (pinned host reads copied
+in chunks inside the timed region, graph statistics read back each step).
+The ``roofline`` object rates the insert kernel alone: algorithmic bytes per
+launch (64 B per vertex touch -- one 32-byte sector read and written -- plus
+the packed reads and offsets) over its CUDA-event duration, against the
+measured HBM copy bandwidth.  ``cpu_baseline`` times the CPU oracle on a
+bounded sample of the same reads.
+
+``--impl reference`` times the CPU oracle itself (the only reference there
+is) on bounded samples of the same workload.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges inserted/s on 1 GB300 + % atomic/HBM roofline; batch p50/p99 latency"
+FALLBACK_HBM_GBS = 6800.0
+SECTOR_RMW_BYTES = 64  # one 32-byte sector read + written per vertex touch
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="100mbp_30x_k31")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def workload_distinct(name):
+    """Distinct vertices of a workload as recorded by the oracle, if known."""
+    p = os.path.join(ROOT, "tests", "golden", "workload_digests.json")
+    if os.path.exists(p):
+        d = json.load(open(p)).get(name)
+        if d:
+            return int(d["n_vertices"])
+    return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for f in ("dbg_insert.cu", "dbg_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2401_02756_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per insert launch from a committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "insert_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload)
+    if not e or e.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = str(gpu_index)
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.idx], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle_sample(rs, seconds_target, threads, seed_reads=20_000):
+    """Time the oracle (as it stands) on a prefix of the reads sized to take
+    about ``seconds_target`` seconds; returns (edges/s, sample description)."""
+    import oracle
+    from paper_2401_02756_gb300 import synth
+
+    def prefix(n):
+        n = min(n, rs.n_reads)
+        nb = int((int(rs.offsets[n]) + 3) // 4)
+        return synth.ReadSet(rs.name, rs.k, rs.packed[:nb], rs.offsets[:n + 1].copy())
+
+    cal = prefix(seed_reads)
+    t = time.perf_counter()
+    oracle.build_graph(cal.packed, cal.offsets, cal.k, threads=threads)
+    dt = max(time.perf_counter() - t, 1e-3)
+    n = int(min(rs.n_reads, max(seed_reads, seed_reads * seconds_target / dt)))
+    smp = prefix(n)
+    t = time.perf_counter()
+    oracle.build_graph(smp.packed, smp.offsets, smp.k, threads=threads)
+    dt = time.perf_counter() - t
+    return smp.n_edges() / dt, dt, n, f"first {n} of {rs.n_reads} reads ({smp.n_edges()} edges), {dt:.1f} s"
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_2401_02756_gb300 import build as _build
+    from paper_2401_02756_gb300 import dbg, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    dbg.load()
+
+    rs = synth.WORKLOADS[args.workload]()
+    edges = rs.n_edges()
+    touches = int(np.maximum(rs.lengths() - rs.k + 2, 0).sum())
+    packed = torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).to(dev)
+    offsets = torch.from_numpy(rs.offsets.view(np.int64).copy()).to(dev)
+
+    D = workload_distinct(args.workload)
+    d_source = "oracle (recorded)"
+    if D is None:  # size the table from a pilot build in a generous table
+        d_source = "pilot build"
+        pilot = dbg.Graph(rs.k, int(touches * 1.05) + 1024)
+        pilot.insert(packed, offsets)
+        D, _ = pilot.stats()
+        pilot.close()
+    capacity = int(math.ceil(1.5 * D))
+    g = dbg.Graph(rs.k, capacity)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        g.reset(stream)
+        g.insert(packed, offsets, stream=stream)
+    torch.cuda.synchronize()
+    st = g.status()
+    if st != dbg.OK:
+        raise RuntimeError(f"warm-up build failed: {dbg.STATUS_NAMES.get(st, st)}")
+    nv, ne = g.stats()
+    if ne != edges or nv != D:
+        raise RuntimeError(f"graph check failed: {nv} vertices / {ne} edges, expected {D} / {edges}")
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)
+    t0.record(stream)
+    for i in range(K):
+        ev[i][0].record(stream)
+        g.reset(stream)
+        ev[i][1].record(stream)
+        g.insert(packed, offsets, stream=stream)
+        ev[i][2].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    if dist:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    k1_ms = [b.elapsed_time(c) for a, b, c in ev]
+    k2_ms = [a.elapsed_time(b) for a, b, c in ev]
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = g.status()
+    if st != dbg.OK:
+        raise RuntimeError(f"timed build failed: {dbg.STATUS_NAMES.get(st, st)}")
+
+    value = edges * K * world / (total_ms / 1e3)
+    k1_mean_s = statistics.mean(k1_ms) / 1e3
+    alg_bytes = touches * SECTOR_RMW_BYTES + rs.packed.nbytes + rs.offsets.nbytes
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / k1_mean_s / 1e9
+    traffic = recorded_traffic(args.workload)
+
+    # measured random-sector ceiling (K5) over a buffer the size of the table
+    probe = None
+    if not args.no_probe:
+        buf = torch.empty(capacity * 32, dtype=torch.uint8, device=dev)
+        buf.zero_()
+        for _ in range(2):
+            dbg.probe_random_sectors(buf, capacity, touches, 7, 1, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for mode in (0, 1):
+            a.record(stream)
+            dbg.probe_random_sectors(buf, capacity, touches, 11 + mode, mode, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        del buf
+        probe = {"touches": touches, "red_only_ms": round(ms[0], 3), "load_red_ms": round(ms[1], 3),
+                 "load_red_touches_per_s": touches / (ms[1] / 1e3),
+                 "load_red_gbs_equiv": touches * SECTOR_RMW_BYTES / (ms[1] / 1e3) / 1e9,
+                 "insert_frac_of_probe": (ms[1] / 1e3) / k1_mean_s}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        pk_h = torch.from_numpy(rs.packed).pin_memory()
+        of_h = torch.from_numpy(rs.offsets.view(np.int64)).pin_memory()
+        g.reset(stream)
+        g.insert_host(pk_h, of_h, stream=stream)
+        g.stats(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        a = time.perf_counter()
+        for _ in range(K):
+            g.reset(stream)
+            g.insert_host(pk_h, of_h, stream=stream)
+            nv_e, ne_e = g.stats(stream)  # device -> host read of the result
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - a
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        if ne_e != edges:
+            raise RuntimeError("end-to-end build lost edges")
+        e2e = {"value": edges * K * world / e2e_s, "unit": "edges/s",
+               "h2d_bytes_per_step": int(rs.packed.nbytes + rs.offsets.nbytes),
+               "d2h_bytes_per_step": 2 * 8 + 4}
+    g.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        v, dt, _, desc = time_oracle_sample(rs, 15.0, cores)
+        cpu = {"value": v, "unit": "edges/s", "cores": cores, "kind": "oracle",
+               "sample": desc + f", {cores} threads (hash-sharded vertices, every thread scans every read)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "genome_bp": rs.meta.get("genome_len"),
+                       "n_reads": rs.n_reads, "read_len": rs.meta.get("read_len"), "k": rs.k,
+                       "error_rate": rs.meta.get("error_rate"), "edges": edges,
+                       "distinct_vertices": D, "distinct_source": d_source,
+                       "capacity_slots": capacity, "table_gb": capacity * 32 / 1e9,
+                       "l2": "table and reads larger than L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}"},
+            "insert_only_edges_per_s": edges / k1_mean_s,
+            "k1_insert_ms": {"mean": statistics.mean(k1_ms), "min": min(k1_ms), "max": max(k1_ms)},
+            "k2_init_ms": statistics.mean(k2_ms),
+            "step_ms_p50": float(np.percentile(step_ms, 50)),
+            "step_ms_p99": float(np.percentile(step_ms, 99)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "alg_bytes_per_launch": alg_bytes,
+                         "alg_bytes_per_edge": alg_bytes / edges},
+            "random_sector_probe": probe,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+            "gpu_launches": 2 * K,
+            "kernel_source_digest": kernel_source_digest(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2401_02756_gb300 import synth
+
+    oracle.build()
+    rs = synth.WORKLOADS[args.workload]()
+    cores = host_cores()
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    # size one step's sample from a calibration run
+    _, _, n, _ = time_oracle_sample(rs, per_step, cores)
+    nb = int((int(rs.offsets[n]) + 3) // 4)
+    smp = synth.ReadSet(rs.name, rs.k, rs.packed[:nb], rs.offsets[:n + 1].copy())
+    for _ in range(args.warmup):
+        oracle.build_graph(smp.packed, smp.offsets, smp.k, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.build_graph(smp.packed, smp.offsets, smp.k, threads=cores)
+        times.append(time.perf_counter() - t)
+    value = smp.n_edges() / statistics.mean(times)
+    sample = (f"first {n} of {rs.n_reads} reads ({smp.n_edges()} edges) per step, "
+              f"{cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "k": rs.k, "n_reads": rs.n_reads},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

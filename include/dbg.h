@@ -1,0 +1,196 @@
+/*
+ * dbg.h -- C ABI of the GB300 A-Bruijn graph builder (libdbg.so, sm_103a).
+ *
+ * The operation is the graph build of "Lock-free de Bruijn graph"
+ * (Gorniak & Nowak, arXiv 2401.02756): every length-k substring
+ * s_0..s_{k-1} of every read is an edge from the vertex s_0..s_{k-2} to the
+ * vertex s_1..s_{k-1} (Section "Background"); both vertices are put in one
+ * shared hash table and the source vertex's counter for the label s_{k-1}
+ * is incremented (Alg. 2 "makeGraph", Alg. 3 "addLeftVertex"; the target is
+ * only made to exist, per the addRightVertex prose after Alg. 3).
+ *
+ * Conventions for every entry point:
+ *   - Return value: a dbg_status code (DBG_OK = 0).  Argument errors are
+ *     returned synchronously and nothing is launched.  Errors found by the
+ *     GPU while a launch runs (table full, bad offsets) are STICKY: they are
+ *     recorded in the handle's device status word and returned by the next
+ *     dbg_get_status, dbg_stats or dbg_export_sorted.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Launching calls are asynchronous and stream-ordered;
+ *     the caller keeps every input alive until the stream has passed the call.
+ *   - Device pointers may come from any allocator (cudaMalloc, a PyTorch
+ *     tensor's data_ptr(), a memory pool).
+ *   - Packed reads: base i of the stream sits in bits [2*(i%4), 2*(i%4)+1] of
+ *     byte i/4, codes A=0, C=1, G=2, T=3.  `offsets` holds n_reads+1
+ *     non-decreasing base positions; read r is [offsets[r], offsets[r+1]).
+ *     offsets[0] may be non-zero.  The packed buffer must be readable for
+ *     ceil(offsets[n_reads] / 4) bytes.  A read shorter than k holds no k-mer
+ *     and adds nothing.
+ *   - Vertex keys: the (k-1) bases of a vertex, 2 bits each, first base in
+ *     the most significant position (so key order is lexicographic order
+ *     with A < C < G < T).  2 <= k <= 32, so a key has at most 62 bits.
+ *   - Counters: 32-bit unsigned, one per label in the order A, C, G, T,
+ *     wrapping modulo 2^32 (the paper's are 8-bit, Section "Graph data
+ *     structure"; the wider width keeps high-coverage repeats exact).
+ */
+#ifndef DBG_H
+#define DBG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dbg_status {
+  DBG_OK = 0,
+  DBG_ERR_INVALID_ARG = 1,      /* bad argument; nothing was launched */
+  DBG_ERR_OOM = 2,              /* a device or host allocation failed */
+  DBG_ERR_CAPACITY = 3,         /* sticky: a vertex found no free slot within max_probes */
+  DBG_ERR_CUDA = 4,             /* a CUDA runtime call failed (see dbg_last_cuda_error) */
+  DBG_ERR_BUFFER_TOO_SMALL = 5, /* export: max_n < number of vertices (n_out tells how many) */
+  DBG_ERR_BAD_OFFSETS = 6       /* sticky: the GPU saw offsets[r+1] < offsets[r] */
+} dbg_status;
+
+typedef struct dbg_graph *dbg_handle;
+
+/* Launch shape of the insert kernel.  Every field may be 0 for "automatic".
+ * The built graph does not depend on these values: only the speed does. */
+typedef struct dbg_tuning {
+  int block_threads;  /* threads per CTA, a multiple of 32 in [64, 1024] (default 256) */
+  int tile_reads;     /* reads staged per tile, in [1, block_threads] (default block_threads) */
+  int grid_ctas;      /* CTAs in the persistent grid (default: SMs x resident CTAs per SM) */
+  int warp_aggregate; /* 1: merge equal keys of a warp with __match_any_sync; 0: off; -1: default */
+} dbg_tuning;
+
+typedef struct dbg_info {
+  int k;
+  uint64_t n_slots;     /* table slots (32 bytes each) */
+  uint64_t table_bytes; /* device bytes held by the table */
+  uint32_t max_probes;  /* slots probed per vertex before DBG_ERR_CAPACITY */
+  int device;           /* CUDA device the table lives on */
+} dbg_info;
+
+/* Create an empty graph for k-mers of length k (2..32) with room for
+ * `capacity` vertices (>= 1).  The table is an open-addressing array of
+ * `capacity` 32-byte slots (replacing the paper's array of N list heads,
+ * Section "Graph data structure", Fig. 2), allocated on the current CUDA
+ * device and emptied before return (synchronously).  *out receives the
+ * handle, which owns the table until dbg_destroy.
+ * Errors: INVALID_ARG (k or capacity out of range, out == NULL), OOM, CUDA. */
+int dbg_create(int k, uint64_t capacity, dbg_handle *out);
+
+/* As dbg_create, with the probe bound: a vertex that finds no matching or
+ * free slot within `max_probes` consecutive slots sets DBG_ERR_CAPACITY
+ * (0 = default: min(n_slots, 8192)). */
+int dbg_create_ex(int k, uint64_t capacity, uint32_t max_probes, dbg_handle *out);
+
+/* Release the table and every buffer the handle owns.  Synchronizes the
+ * device first.  NULL is ignored. */
+void dbg_destroy(dbg_handle h);
+
+/* Empty the graph (every slot EMPTY, every counter 0) and clear the sticky
+ * status, stream-ordered.  Errors: INVALID_ARG, CUDA. */
+int dbg_reset(dbg_handle h, void *stream);
+
+/* Set the insert kernel's launch shape (NULL restores the defaults).
+ * Errors: INVALID_ARG for out-of-range fields. */
+int dbg_set_tuning(dbg_handle h, const dbg_tuning *t);
+
+/* Fill *out with the handle's parameters. */
+int dbg_get_info(dbg_handle h, dbg_info *out);
+
+/* Insert every k-mer of n_reads reads (Alg. 2 "makeGraph" with Alg. 3 and
+ * the addRightVertex prose): for each length-k substring, find or claim the
+ * prefix vertex and count the label s_{k-1}, and find or claim the suffix
+ * vertex.  `packed` and `offsets` are DEVICE pointers (see the conventions
+ * above); one kernel is launched on `stream`.  Calls on one handle may be
+ * issued from several streams at once: counts add, so the graph does not
+ * depend on the order.  n_reads == 0 launches nothing.
+ * Errors: INVALID_ARG (NULL handle, NULL pointer with n_reads > 0), CUDA;
+ * sticky CAPACITY / BAD_OFFSETS. */
+int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                     uint64_t n_reads, void *stream);
+
+/* As dbg_insert_reads, with `packed` and `offsets` in HOST memory (pinned
+ * memory gives asynchronous copies; pageable memory works but copies are
+ * staged by the driver).  The reads are copied to device staging buffers
+ * owned by the handle in chunks, each chunk's copy overlapping the previous
+ * chunk's insert.  Returns after the last chunk has been launched; the host
+ * buffers may be reused once `stream` has passed the call.
+ * Errors: as dbg_insert_reads, plus OOM for the staging buffers. */
+int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                          uint64_t n_reads, void *stream);
+
+/* One item of a batched insert: a target graph and its reads (device
+ * pointers, same conventions as dbg_insert_reads). */
+typedef struct dbg_batch_item {
+  dbg_handle graph;
+  const uint8_t *packed;
+  const uint64_t *offsets;
+  uint64_t n_reads;
+} dbg_batch_item;
+
+/* Insert many independent read sets, each into its own graph (graphs may
+ * differ in k and size), with ONE kernel launch on `stream` whose CTAs take
+ * (item, read tile) work units from a shared queue.  Every graph must live
+ * on the current device.  The result equals one dbg_insert_reads per item.
+ * Errors: INVALID_ARG, OOM (descriptor upload), CUDA; sticky errors are
+ * recorded in each item's own graph. */
+int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *stream);
+
+/* Wait for `stream`, then return the sticky status (DBG_OK, CAPACITY or
+ * BAD_OFFSETS), or CUDA if a launch failed. */
+int dbg_get_status(dbg_handle h, void *stream);
+
+/* Wait for `stream`, then count the vertices and the edges (the sum of all
+ * counters) of the graph.  Either output pointer may be NULL.
+ * Returns the sticky status when it is not DBG_OK (outputs still written). */
+int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *stream);
+
+/* Export the graph sorted by key (ascending, i.e. lexicographic with
+ * A<C<G<T): keys_out[i] and counts_out[4*i .. 4*i+3] (labels A, C, G, T).
+ * Output pointers may be host or device memory (copied with
+ * cudaMemcpyDefault); either may be NULL to skip it.  Waits for `stream`.
+ * *n_out receives the number of vertices D.  If D > max_n nothing is
+ * written and DBG_ERR_BUFFER_TOO_SMALL is returned (a call with max_n = 0
+ * is therefore a size query).  Temporary device memory (about 48 bytes per
+ * vertex) is taken from the stream-ordered allocator and released before
+ * return.  Errors: INVALID_ARG, OOM, CUDA, BUFFER_TOO_SMALL, and the sticky
+ * status (nothing exported when it is set). */
+int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, uint64_t max_n,
+                      uint64_t *n_out, void *stream);
+
+/* Host helper: pack n ASCII bases (A, C, G, T; upper case) into out, which
+ * holds ceil(n/4) bytes, starting at base position `phase` (0..3) of out[0]
+ * (bits of out[0] below the phase are preserved).  Any other symbol returns
+ * INVALID_ARG and *bad_index (if not NULL) receives its position; 2-bit
+ * packing cannot represent N. */
+int dbg_pack_ascii(const char *ascii, uint64_t n, uint8_t *out, int phase, uint64_t *bad_index);
+
+/* Message for a status code (static storage). */
+const char *dbg_strerror(int code);
+
+/* Text of the last CUDA error seen by this library on this thread ("" if none). */
+const char *dbg_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement kernels: the random-sector ceiling the insert is rated on.   */
+/* ------------------------------------------------------------------------ */
+
+/* Random 32-byte-sector traffic over `n_slots` 32-byte slots at `buf`
+ * (device, 32-byte aligned): `n_ops` operations at slots drawn by a
+ * counter-based hash of (seed, op index).  mode 0: atomicAdd to one 32-bit
+ * word of the slot (read-modify-write at L2, no return); mode 1: load the
+ * slot's first 8 bytes, then atomicAdd to a word of the same slot (the
+ * insert's found-vertex pattern); mode 2: atomicCAS on the first 8 bytes.
+ * The buffer's contents change.  Errors: INVALID_ARG, CUDA. */
+int dbg_probe_random_sectors(void *buf, uint64_t n_slots, uint64_t n_ops, uint64_t seed, int mode,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBG_H */

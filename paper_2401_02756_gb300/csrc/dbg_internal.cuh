@@ -1,0 +1,149 @@
+// Internal definitions of libdbg: the device table layout, the item
+// descriptor the insert kernel consumes, and the handle.
+//
+// Table (replaces the paper's array of N atomic list heads with chained
+// Nodes, Section "Graph data structure", Fig. 2): an open-addressing array of
+// 32-byte slots, one slot per 32-byte DRAM sector, so that a vertex touch --
+// claim, find and count -- is one sector.  A slot holds the vertex key (the
+// paper's stored (k-1)-mer, here 2 bits per base) and the four out-edge
+// counters; the paper's four edge pointers are not stored, because the
+// target of label b from key v is ((v << 2) | b) masked to 2(k-1) bits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dbg.h"
+
+namespace dbg {
+
+constexpr unsigned long long kEmpty = ~0ull;  // never a key: keys have <= 62 bits
+constexpr uint32_t kDefaultMaxProbes = 8192;
+
+struct __align__(32) Slot {
+  unsigned long long key;  // kEmpty or the vertex key
+  uint32_t cnt[4];         // out-edge counters, labels A, C, G, T
+  uint32_t pad[2];         // zero; keeps one slot per 32-byte sector
+};
+static_assert(sizeof(Slot) == 32, "slot must be one 32-byte sector");
+
+// One read set to insert into one table (a batch is an array of these).
+struct ItemDesc {
+  const uint8_t *packed;     // 2-bit stream, byte 0 holds base `origin`
+  const uint64_t *offsets;   // n_reads + 1 base positions
+  uint64_t n_reads;
+  uint64_t origin;           // base position of packed[0] (multiple of 4)
+  Slot *table;
+  uint64_t n_slots;
+  uint32_t *status;          // sticky device status word
+  uint32_t max_probes;
+  int k;
+  uint64_t tile_begin;       // first global tile index of this item
+  int vec_ok;                // packed is 16-byte aligned: vector loads allowed
+  int pad_;
+};
+
+// MurmurHash3's 64-bit finalizer (Appleby, public domain): a bijective mix
+// so that nearby keys land on unrelated slots.
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t home_slot(uint64_t key, uint64_t n_slots) {
+  return __umul64hi(fmix64(key), n_slots);
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
+  return *(const volatile uint32_t *)p;
+}
+
+__device__ __forceinline__ void set_sticky(uint32_t *status, uint32_t code) {
+  atomicCAS(status, 0u, code);
+}
+
+// Reverse the order of the 32 two-bit groups of a 64-bit word.
+__device__ __forceinline__ uint64_t reverse_pairs(uint64_t x) {
+  x = __brevll(x);
+  return ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+}
+
+// Key of the m bases starting at base q of a little-endian 2-bit stream whose
+// 64-bit words (32 bases each) are w[]: first base most significant.
+__device__ __forceinline__ uint64_t key_from_words(uint64_t lo, uint64_t hi, uint32_t sh, int m) {
+  uint64_t x = sh ? ((lo >> sh) | (hi << (64u - sh))) : lo;
+  return reverse_pairs(x) >> (64 - 2 * m);
+}
+
+}  // namespace dbg
+
+// The handle.
+struct dbg_graph {
+  int k = 0;
+  int device = 0;
+  uint64_t n_slots = 0;
+  uint32_t max_probes = 0;
+  dbg::Slot *table = nullptr;
+  uint32_t *d_status = nullptr;
+  unsigned long long *d_acc = nullptr;  // [2]: vertices, edges (stats)
+  dbg_tuning tuning{};                  // as set by the user (0 = auto)
+  int sm_count = 0;
+  // staging for dbg_insert_reads_host
+  uint8_t *stage_packed[2] = {nullptr, nullptr};
+  uint64_t *stage_offsets[2] = {nullptr, nullptr};
+  uint64_t stage_packed_bytes = 0;
+  uint64_t stage_offsets_count = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+};
+
+namespace dbg {
+
+// Error plumbing shared by the entry points (host side).
+int cuda_fail(cudaError_t e, const char *what);
+#define DBG_CK(call)                                        \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return dbg::cuda_fail(e_, #call); \
+  } while (0)
+
+// Fill an ItemDesc for a handle and a read set.
+ItemDesc make_item(dbg_handle h, const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads,
+                   uint64_t origin);
+
+// Items passed to one insert launch by value (kernel parameter space), so a
+// launch needs no descriptor upload.  N = 1 for a single read set; batches
+// are cut into launches of at most kBatchItems items.
+constexpr int kBatchItems = 128;
+template <int N>
+struct ItemPack {
+  int n_items;
+  int pad_;
+  uint64_t total_tiles;
+  ItemDesc d[N];
+};
+
+// Launch the insert kernel over host-side descriptors items[0..n_items)
+// (tile_begin already set, total_tiles their sum); n_items <= kBatchItems.
+int launch_insert(const ItemDesc *items, int n_items, uint64_t total_tiles,
+                  const dbg_tuning &tuning, int sm_count, cudaStream_t stream);
+
+// Resolved tuning (defaults filled in).
+dbg_tuning resolve_tuning(const dbg_tuning &t);
+
+// Table kernels.
+int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream);
+int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, cudaStream_t stream);
+
+}  // namespace dbg

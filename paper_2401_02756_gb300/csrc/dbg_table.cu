@@ -1,0 +1,452 @@
+// Handle lifecycle, table kernels (K2 init, stats) and the host-side entry
+// points of the C ABI declared in include/dbg.h.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "dbg_internal.cuh"
+
+namespace dbg {
+
+static thread_local char g_last_error[512];
+
+int cuda_fail(cudaError_t e, const char *what) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
+           cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DBG_ERR_OOM : DBG_ERR_CUDA;
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) {
+      err = cudaSetDevice(dev);
+      changed = err == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+// K2: every slot EMPTY with zero counters; two 16-byte stores per slot.
+__global__ void k_table_init(uint4 *t, uint64_t n_vec) {
+  const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
+  const uint4 tail = make_uint4(0u, 0u, 0u, 0u);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vec; i += stride)
+    t[i] = (i & 1) ? tail : head;
+}
+
+// Vertices (occupied slots) and edges (sum of counters) of a table.
+__global__ void k_stats(const Slot *t, uint64_t n_slots, unsigned long long *acc) {
+  unsigned long long nv = 0, ne = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += stride) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(t + i);
+    const uint4 a = __ldcs(p), b = __ldcs(p + 1);
+    const unsigned long long key = (unsigned long long)a.x | ((unsigned long long)a.y << 32);
+    if (key != kEmpty) {
+      nv += 1;
+      ne += (unsigned long long)a.z + a.w + b.x + b.y;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    nv += __shfl_down_sync(0xffffffffu, nv, d);
+    ne += __shfl_down_sync(0xffffffffu, ne, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, nv);
+    atomicAdd(acc + 1, ne);
+  }
+}
+
+int stream_grid(int sm_count, int per_sm) { return std::max(1, sm_count) * per_sm; }
+
+}  // namespace
+
+int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  DBG_CK(cudaGetDevice(&dev));
+  DBG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const uint64_t n_vec = n_slots * 2;
+  uint64_t want = (n_vec + 255) / 256;
+  const int grid = (int)std::min<uint64_t>(want, (uint64_t)stream_grid(sms, 8));
+  k_table_init<<<std::max(grid, 1), 256, 0, stream>>>(reinterpret_cast<uint4 *>(table), n_vec);
+  DBG_CK(cudaGetLastError());
+  return DBG_OK;
+}
+
+int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  DBG_CK(cudaGetDevice(&dev));
+  DBG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DBG_CK(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), stream));
+  const uint64_t want = (n_slots + 255) / 256;
+  const int grid = (int)std::min<uint64_t>(want, (uint64_t)stream_grid(sms, 8));
+  k_stats<<<std::max(grid, 1), 256, 0, stream>>>(table, n_slots, acc);
+  DBG_CK(cudaGetLastError());
+  return DBG_OK;
+}
+
+ItemDesc make_item(dbg_handle h, const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads,
+                   uint64_t origin) {
+  ItemDesc it{};
+  it.packed = packed;
+  it.offsets = offsets;
+  it.n_reads = n_reads;
+  it.origin = origin;
+  it.table = h->table;
+  it.n_slots = h->n_slots;
+  it.status = h->d_status;
+  it.max_probes = h->max_probes;
+  it.k = h->k;
+  it.tile_begin = 0;
+  it.vec_ok = ((uintptr_t)packed & 15u) == 0 ? 1 : 0;
+  return it;
+}
+
+}  // namespace dbg
+
+using dbg::DeviceGuard;
+
+// ---------------------------------------------------------------------------
+// lifecycle
+// ---------------------------------------------------------------------------
+
+extern "C" int dbg_create_ex(int k, uint64_t capacity, uint32_t max_probes, dbg_handle *out) {
+  if (!out) return DBG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (k < 2 || k > 32 || capacity == 0 || capacity > (~0ull / sizeof(dbg::Slot)))
+    return DBG_ERR_INVALID_ARG;
+  dbg_graph *h = new (std::nothrow) dbg_graph();
+  if (!h) return DBG_ERR_OOM;
+  h->k = k;
+  h->n_slots = capacity;
+  h->max_probes = max_probes ? max_probes
+                             : (uint32_t)std::min<uint64_t>(capacity, dbg::kDefaultMaxProbes);
+  int st = DBG_OK;
+  do {
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaGetDevice"); break; }
+    e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaDeviceGetAttribute"); break; }
+    e = cudaMalloc(&h->table, capacity * sizeof(dbg::Slot));
+    if (e != cudaSuccess) { h->table = nullptr; st = dbg::cuda_fail(e, "cudaMalloc(table)"); break; }
+    void *small = nullptr;
+    e = cudaMalloc(&small, 64);
+    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaMalloc(status)"); break; }
+    h->d_status = static_cast<uint32_t *>(small);
+    h->d_acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 16);
+    e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaStreamCreate"); break; }
+    for (int i = 0; i < 2 && st == DBG_OK; ++i) {
+      e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_consumed[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) st = dbg::cuda_fail(e, "cudaEventCreate");
+    }
+    if (st != DBG_OK) break;
+    st = dbg::launch_table_init(h->table, h->n_slots, h->copy_stream);
+    if (st != DBG_OK) break;
+    e = cudaMemsetAsync(h->d_status, 0, 64, h->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_stream);
+    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "table init"); break; }
+  } while (0);
+  if (st != DBG_OK) {
+    dbg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return DBG_OK;
+}
+
+extern "C" int dbg_create(int k, uint64_t capacity, dbg_handle *out) {
+  return dbg_create_ex(k, capacity, 0, out);
+}
+
+extern "C" void dbg_destroy(dbg_handle h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  cudaFree(h->table);
+  cudaFree(h->d_status);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->stage_packed[i]);
+    cudaFree(h->stage_offsets[i]);
+    if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+    if (h->ev_consumed[i]) cudaEventDestroy(h->ev_consumed[i]);
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  delete h;
+}
+
+extern "C" int dbg_reset(dbg_handle h, void *stream) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = dbg::launch_table_init(h->table, h->n_slots, s);
+  if (st != DBG_OK) return st;
+  DBG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s));
+  return DBG_OK;
+}
+
+extern "C" int dbg_set_tuning(dbg_handle h, const dbg_tuning *t) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  if (!t) {
+    h->tuning = dbg_tuning{};
+    return DBG_OK;
+  }
+  dbg_tuning r = *t;
+  if (r.block_threads != 0 && r.block_threads != 128 && r.block_threads != 256 &&
+      r.block_threads != 512)
+    return DBG_ERR_INVALID_ARG;
+  const int bt = r.block_threads ? r.block_threads : 256;
+  if (r.tile_reads < 0 || r.tile_reads > bt) return DBG_ERR_INVALID_ARG;
+  if (r.grid_ctas < 0) return DBG_ERR_INVALID_ARG;
+  if (r.warp_aggregate < -1 || r.warp_aggregate > 1) return DBG_ERR_INVALID_ARG;
+  h->tuning = r;
+  return DBG_OK;
+}
+
+extern "C" int dbg_get_info(dbg_handle h, dbg_info *out) {
+  if (!h || !out) return DBG_ERR_INVALID_ARG;
+  out->k = h->k;
+  out->n_slots = h->n_slots;
+  out->table_bytes = h->n_slots * sizeof(dbg::Slot);
+  out->max_probes = h->max_probes;
+  out->device = h->device;
+  return DBG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// inserts
+// ---------------------------------------------------------------------------
+
+extern "C" int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                                uint64_t n_reads, void *stream) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  if (n_reads == 0) return DBG_OK;
+  if (!packed || !offsets) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  const dbg_tuning t = dbg::resolve_tuning(h->tuning);
+  const uint64_t tiles = (n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
+  const dbg::ItemDesc it = dbg::make_item(h, packed, offsets, n_reads, 0);
+  return dbg::launch_insert(&it, 1, tiles, h->tuning, h->sm_count,
+                            static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+constexpr uint64_t kStageBytes = 64ull << 20;   // packed bytes per host chunk
+constexpr uint64_t kStageReads = 1ull << 20;    // reads per host chunk
+
+int grow_stage(dbg_handle h, uint64_t bytes, uint64_t reads) {
+  if (bytes > h->stage_packed_bytes) {
+    DBG_CK(cudaStreamSynchronize(h->copy_stream));
+    DBG_CK(cudaDeviceSynchronize());
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(h->stage_packed[i]);
+      h->stage_packed[i] = nullptr;
+    }
+    h->stage_packed_bytes = 0;
+    for (int i = 0; i < 2; ++i) {
+      cudaError_t e = cudaMalloc(&h->stage_packed[i], bytes);
+      if (e != cudaSuccess) return dbg::cuda_fail(e, "cudaMalloc(staging)");
+    }
+    h->stage_packed_bytes = bytes;
+  }
+  if (reads + 1 > h->stage_offsets_count) {
+    DBG_CK(cudaDeviceSynchronize());
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(h->stage_offsets[i]);
+      h->stage_offsets[i] = nullptr;
+    }
+    h->stage_offsets_count = 0;
+    for (int i = 0; i < 2; ++i) {
+      cudaError_t e = cudaMalloc(&h->stage_offsets[i], (reads + 1) * sizeof(uint64_t));
+      if (e != cudaSuccess) return dbg::cuda_fail(e, "cudaMalloc(staging)");
+    }
+    h->stage_offsets_count = reads + 1;
+  }
+  return DBG_OK;
+}
+
+}  // namespace
+
+extern "C" int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                                     uint64_t n_reads, void *stream) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  if (n_reads == 0) return DBG_OK;
+  if (!packed || !offsets) return DBG_ERR_INVALID_ARG;
+  for (uint64_t r = 0; r < n_reads; ++r)
+    if (offsets[r + 1] < offsets[r]) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const dbg_tuning t = dbg::resolve_tuning(h->tuning);
+
+  // chunk boundaries: at most kStageReads reads and about kStageBytes bytes
+  std::vector<uint64_t> cuts{0};
+  uint64_t max_bytes = 0, max_reads = 0;
+  for (uint64_t r0 = 0; r0 < n_reads;) {
+    const uint64_t b0 = offsets[r0] >> 2;
+    uint64_t r1 = std::min(n_reads, r0 + kStageReads);
+    // shrink until the chunk's bytes fit (always keep at least one read)
+    uint64_t lo = r0 + 1, hi = r1;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi + 1) / 2;
+      if (((offsets[mid] + 3) >> 2) - b0 <= kStageBytes)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    r1 = lo;
+    max_bytes = std::max(max_bytes, ((offsets[r1] + 3) >> 2) - b0);
+    max_reads = std::max(max_reads, r1 - r0);
+    cuts.push_back(r1);
+    r0 = r1;
+  }
+  int st = grow_stage(h, std::max<uint64_t>(16, (max_bytes + 15) & ~15ull), max_reads);
+  if (st != DBG_OK) return st;
+
+  for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+    const int b = (int)(c & 1);
+    const uint64_t r0 = cuts[c], r1 = cuts[c + 1];
+    const uint64_t byte0 = offsets[r0] >> 2;
+    const uint64_t nbytes = ((offsets[r1] + 3) >> 2) - byte0;
+    DBG_CK(cudaStreamWaitEvent(h->copy_stream, h->ev_consumed[b], 0));
+    DBG_CK(cudaMemcpyAsync(h->stage_offsets[b], offsets + r0, (r1 - r0 + 1) * sizeof(uint64_t),
+                           cudaMemcpyHostToDevice, h->copy_stream));
+    if (nbytes)
+      DBG_CK(cudaMemcpyAsync(h->stage_packed[b], packed + byte0, nbytes, cudaMemcpyHostToDevice,
+                             h->copy_stream));
+    DBG_CK(cudaEventRecord(h->ev_copied[b], h->copy_stream));
+    DBG_CK(cudaStreamWaitEvent(s, h->ev_copied[b], 0));
+    const dbg::ItemDesc it =
+        dbg::make_item(h, h->stage_packed[b], h->stage_offsets[b], r1 - r0, byte0 * 4);
+    const uint64_t tiles = (r1 - r0 + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
+    st = dbg::launch_insert(&it, 1, tiles, h->tuning, h->sm_count, s);
+    if (st != DBG_OK) return st;
+    DBG_CK(cudaEventRecord(h->ev_consumed[b], s));
+  }
+  return DBG_OK;
+}
+
+extern "C" int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *stream) {
+  if (n_items < 0 || (n_items > 0 && !items)) return DBG_ERR_INVALID_ARG;
+  if (n_items == 0) return DBG_OK;
+  const int dev = items[0].graph ? items[0].graph->device : -1;
+  for (int i = 0; i < n_items; ++i) {
+    if (!items[i].graph || items[i].graph->device != dev) return DBG_ERR_INVALID_ARG;
+    if (items[i].n_reads > 0 && (!items[i].packed || !items[i].offsets)) return DBG_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(dev);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const dbg_tuning t = dbg::resolve_tuning(items[0].graph->tuning);
+  // one launch per group of up to kBatchItems non-empty items
+  std::vector<dbg::ItemDesc> group;
+  group.reserve(dbg::kBatchItems);
+  uint64_t tiles = 0;
+  for (int i = 0; i <= n_items; ++i) {
+    const bool flush = (i == n_items) || (int)group.size() == dbg::kBatchItems;
+    if (flush && !group.empty()) {
+      const int st = dbg::launch_insert(group.data(), (int)group.size(), tiles, t,
+                                        items[0].graph->sm_count, s);
+      if (st != DBG_OK) return st;
+      group.clear();
+      tiles = 0;
+    }
+    if (i == n_items) break;
+    if (items[i].n_reads == 0) continue;
+    dbg::ItemDesc it = dbg::make_item(items[i].graph, items[i].packed, items[i].offsets,
+                                      items[i].n_reads, 0);
+    it.tile_begin = tiles;
+    tiles += (items[i].n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
+    group.push_back(it);
+  }
+  return DBG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// status and stats
+// ---------------------------------------------------------------------------
+
+extern "C" int dbg_get_status(dbg_handle h, void *stream) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t st = 0;
+  DBG_CK(cudaMemcpyAsync(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaStreamSynchronize(s));
+  return (int)st;
+}
+
+extern "C" int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *stream) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = dbg::launch_stats(h->table, h->n_slots, h->d_acc, s);
+  if (st != DBG_OK) return st;
+  unsigned long long acc[2] = {0, 0};
+  uint32_t status = 0;
+  DBG_CK(cudaMemcpyAsync(acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaStreamSynchronize(s));
+  if (n_vertices) *n_vertices = acc[0];
+  if (n_edges) *n_edges = acc[1];
+  return (int)status;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+
+extern "C" int dbg_pack_ascii(const char *ascii, uint64_t n, uint8_t *out, int phase,
+                              uint64_t *bad_index) {
+  if ((n > 0 && (!ascii || !out)) || phase < 0 || phase > 3) return DBG_ERR_INVALID_ARG;
+  for (uint64_t i = 0; i < n; ++i) {
+    unsigned code;
+    switch (ascii[i]) {
+      case 'A': code = 0; break;
+      case 'C': code = 1; break;
+      case 'G': code = 2; break;
+      case 'T': code = 3; break;
+      default:
+        if (bad_index) *bad_index = i;
+        return DBG_ERR_INVALID_ARG;
+    }
+    const uint64_t p = i + (uint64_t)phase;
+    const unsigned sh = 2u * (unsigned)(p & 3u);
+    uint8_t &byte = out[p >> 2];
+    byte = (uint8_t)((byte & ~(3u << sh)) | (code << sh));
+  }
+  return DBG_OK;
+}
+
+extern "C" const char *dbg_strerror(int code) {
+  switch (code) {
+    case DBG_OK: return "ok";
+    case DBG_ERR_INVALID_ARG: return "invalid argument";
+    case DBG_ERR_OOM: return "out of memory";
+    case DBG_ERR_CAPACITY: return "table full: a vertex found no free slot within max_probes";
+    case DBG_ERR_CUDA: return "CUDA error";
+    case DBG_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
+    case DBG_ERR_BAD_OFFSETS: return "offsets are not non-decreasing";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char *dbg_last_cuda_error(void) { return dbg::g_last_error; }

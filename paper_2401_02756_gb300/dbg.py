@@ -1,0 +1,275 @@
+"""Thin ctypes binding of ``libdbg.so`` (the C ABI in ``include/dbg.h``).
+
+Argument marshalling only: every step of the graph build runs in the
+library's CUDA kernels.  Device buffers are passed as PyTorch CUDA tensors
+(or anything with ``data_ptr()``), host buffers as numpy arrays, and streams
+as ``torch.cuda.Stream`` objects or raw ``cudaStream_t`` integers
+(``None`` = PyTorch's current stream).  The library must have been built
+(``paper_2401_02756_gb300.build.build()``); there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdbg.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_BUFFER_TOO_SMALL, ERR_BAD_OFFSETS = range(7)
+STATUS_NAMES = {0: "DBG_OK", 1: "DBG_ERR_INVALID_ARG", 2: "DBG_ERR_OOM", 3: "DBG_ERR_CAPACITY",
+                4: "DBG_ERR_CUDA", 5: "DBG_ERR_BUFFER_TOO_SMALL", 6: "DBG_ERR_BAD_OFFSETS"}
+
+EXPORTED = [
+    "dbg_create", "dbg_create_ex", "dbg_destroy", "dbg_reset", "dbg_set_tuning", "dbg_get_info",
+    "dbg_insert_reads", "dbg_insert_reads_host", "dbg_insert_batch", "dbg_get_status", "dbg_stats",
+    "dbg_export_sorted", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
+    "dbg_probe_random_sectors",
+]
+
+
+class DbgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {STATUS_NAMES.get(code, code)} ({_strerror(code)})"
+        if code == ERR_CUDA:
+            msg += f" [{last_cuda_error()}]"
+        super().__init__(msg)
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int), ("tile_reads", ctypes.c_int),
+                ("grid_ctas", ctypes.c_int), ("warp_aggregate", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_slots", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
+                ("max_probes", ctypes.c_uint32), ("device", ctypes.c_int)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("packed", ctypes.c_void_p),
+                ("offsets", ctypes.c_void_p), ("n_reads", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libdbg.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: call paper_2401_02756_gb300.build.build() "
+                           "(needs nvcc); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    sig = {
+        "dbg_create": (I, [I, U64, ctypes.POINTER(P)]),
+        "dbg_create_ex": (I, [I, U64, U32, ctypes.POINTER(P)]),
+        "dbg_destroy": (None, [P]),
+        "dbg_reset": (I, [P, P]),
+        "dbg_set_tuning": (I, [P, ctypes.POINTER(Tuning)]),
+        "dbg_get_info": (I, [P, ctypes.POINTER(Info)]),
+        "dbg_insert_reads": (I, [P, P, P, U64, P]),
+        "dbg_insert_reads_host": (I, [P, P, P, U64, P]),
+        "dbg_insert_batch": (I, [ctypes.POINTER(BatchItem), I, P]),
+        "dbg_get_status": (I, [P, P]),
+        "dbg_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
+        "dbg_export_sorted": (I, [P, P, P, U64, ctypes.POINTER(U64), P]),
+        "dbg_pack_ascii": (I, [ctypes.c_char_p, U64, P, I, ctypes.POINTER(U64)]),
+        "dbg_strerror": (ctypes.c_char_p, [I]),
+        "dbg_last_cuda_error": (ctypes.c_char_p, []),
+        "dbg_probe_random_sectors": (I, [P, U64, U64, U64, I, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load().dbg_strerror(code).decode()
+    except Exception:  # pragma: no cover - only when the library is missing
+        return "?"
+
+
+def last_cuda_error() -> str:
+    return load().dbg_last_cuda_error().decode()
+
+
+def _check(code: int, what: str) -> None:
+    if code != OK:
+        raise DbgError(code, what)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return getattr(stream, "cuda_stream", None) or None
+
+
+def _dptr(x) -> int:
+    """Device pointer of a CUDA tensor (or an int)."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "is_cuda") and not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return int(x.data_ptr())
+
+
+def _hptr(a: np.ndarray) -> int:
+    if not isinstance(a, np.ndarray):
+        a = np.asarray(a)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host array must be contiguous")
+    return int(a.ctypes.data) if a.size else 0
+
+
+def _host_view(x, dtype):
+    """numpy view of a host buffer (numpy array or CPU tensor, pinned or not)."""
+    if hasattr(x, "numpy"):
+        return x.numpy().view(dtype)
+    return np.ascontiguousarray(x).view(dtype)
+
+
+class Graph:
+    """An A-Bruijn graph under construction, held in device memory."""
+
+    def __init__(self, k: int, capacity: int, max_probes: int = 0):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.dbg_create_ex(int(k), int(capacity), int(max_probes), ctypes.byref(h)), "dbg_create")
+        self._h = h
+        self.k = int(k)
+
+    # -- lifecycle ----------------------------------------------------------
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise ValueError("graph is closed")
+        return self._h.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            load().dbg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration ------------------------------------------------------
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().dbg_get_info(self.handle, ctypes.byref(inf)), "dbg_get_info")
+        return {"k": inf.k, "n_slots": inf.n_slots, "table_bytes": inf.table_bytes,
+                "max_probes": inf.max_probes, "device": inf.device}
+
+    def set_tuning(self, block_threads: int = 0, tile_reads: int = 0, grid_ctas: int = 0,
+                   warp_aggregate: int = -1) -> None:
+        t = Tuning(block_threads, tile_reads, grid_ctas, warp_aggregate)
+        _check(load().dbg_set_tuning(self.handle, ctypes.byref(t)), "dbg_set_tuning")
+
+    # -- build --------------------------------------------------------------
+    def reset(self, stream=None) -> None:
+        _check(load().dbg_reset(self.handle, _stream(stream)), "dbg_reset")
+
+    def insert(self, packed, offsets, n_reads: int | None = None, stream=None) -> None:
+        """Insert reads held in device memory (``packed`` uint8, ``offsets``
+        int64/uint64 with n_reads + 1 entries)."""
+        if n_reads is None:
+            n_reads = int(offsets.numel()) - 1
+        _check(load().dbg_insert_reads(self.handle, _dptr(packed) or None, _dptr(offsets) or None,
+                                       int(n_reads), _stream(stream)), "dbg_insert_reads")
+
+    def insert_host(self, packed, offsets, stream=None) -> None:
+        """Insert reads held in host memory (copied by the library, in chunks)."""
+        pk = _host_view(packed, np.uint8)
+        of = _host_view(offsets, np.uint64)
+        _check(load().dbg_insert_reads_host(self.handle, _hptr(pk) or None, _hptr(of) or None,
+                                            int(of.size) - 1, _stream(stream)),
+               "dbg_insert_reads_host")
+
+    # -- results ------------------------------------------------------------
+    def status(self, stream=None) -> int:
+        return int(load().dbg_get_status(self.handle, _stream(stream)))
+
+    def stats(self, stream=None) -> tuple[int, int]:
+        nv, ne = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().dbg_stats(self.handle, ctypes.byref(nv), ctypes.byref(ne), _stream(stream)),
+               "dbg_stats")
+        return int(nv.value), int(ne.value)
+
+    def export(self, stream=None) -> tuple[np.ndarray, np.ndarray]:
+        """Sorted vertices: keys (uint64 [D]) and counters (uint32 [D, 4], A C G T)."""
+        L = load()
+        n = ctypes.c_uint64()
+        st = L.dbg_export_sorted(self.handle, None, None, 0, ctypes.byref(n), _stream(stream))
+        if st not in (OK, ERR_BUFFER_TOO_SMALL):
+            raise DbgError(st, "dbg_export_sorted")
+        D = int(n.value)
+        keys = np.empty(D, dtype=np.uint64)
+        counts = np.empty((D, 4), dtype=np.uint32)
+        if D:
+            _check(L.dbg_export_sorted(self.handle, keys.ctypes.data, counts.ctypes.data, D,
+                                       ctypes.byref(n), _stream(stream)), "dbg_export_sorted")
+        return keys, counts
+
+    def export_device(self, stream=None):
+        """Sorted vertices as CUDA tensors (int64 keys [D], int32 counters [D, 4])."""
+        import torch
+        L = load()
+        n = ctypes.c_uint64()
+        st = L.dbg_export_sorted(self.handle, None, None, 0, ctypes.byref(n), _stream(stream))
+        if st not in (OK, ERR_BUFFER_TOO_SMALL):
+            raise DbgError(st, "dbg_export_sorted")
+        D = int(n.value)
+        keys = torch.empty(D, dtype=torch.int64, device="cuda")
+        counts = torch.empty((D, 4), dtype=torch.int32, device="cuda")
+        if D:
+            _check(L.dbg_export_sorted(self.handle, keys.data_ptr(), counts.data_ptr(), D,
+                                       ctypes.byref(n), _stream(stream)), "dbg_export_sorted")
+        return keys, counts
+
+
+def insert_batch(items, stream=None) -> None:
+    """``items``: list of ``(graph, packed, offsets)`` with device buffers."""
+    arr = (BatchItem * max(1, len(items)))()
+    for i, (g, pk, of) in enumerate(items):
+        arr[i] = BatchItem(g.handle, _dptr(pk) or None, _dptr(of) or None, int(of.numel()) - 1)
+    _check(load().dbg_insert_batch(arr, len(items), _stream(stream)), "dbg_insert_batch")
+
+
+def probe_random_sectors(buf, n_slots: int, n_ops: int, seed: int, mode: int, stream=None) -> None:
+    _check(load().dbg_probe_random_sectors(_dptr(buf), int(n_slots), int(n_ops), int(seed),
+                                           int(mode), _stream(stream)), "dbg_probe_random_sectors")
+
+
+def pack_ascii(seq: str, phase: int = 0) -> np.ndarray:
+    """Pack ACGT text with the library's host helper (raises on other symbols)."""
+    b = seq.encode("ascii")
+    out = np.zeros((len(b) + phase + 3) // 4, dtype=np.uint8)
+    bad = ctypes.c_uint64()
+    st = load().dbg_pack_ascii(b, len(b), out.ctypes.data if out.size else None, phase,
+                               ctypes.byref(bad))
+    if st != OK:
+        raise DbgError(st, f"dbg_pack_ascii (symbol at {bad.value})")
+    return out

@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads and exports every symbol that
+include/dbg.h declares; host-only entry points behave (no GPU needed)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2401_02756_gb300 import build, dbg, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return dbg.load()
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(dbg_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = declared_functions()
+    assert "dbg_insert_reads" in decl and "dbg_export_sorted" in decl
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(decl) == sorted(dbg.EXPORTED)
+
+
+def test_library_is_built_for_sm103a(lib):
+    # the cubin's architecture is recorded in the ELF note section names
+    data = open(dbg.LIB_PATH, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_strerror_and_status_names(lib):
+    for code, name in dbg.STATUS_NAMES.items():
+        assert lib.dbg_strerror(code)
+    assert lib.dbg_strerror(99) == b"unknown status"
+
+
+def test_pack_ascii_matches_generator_packing(lib):
+    rng = np.random.default_rng(5)
+    for n in (0, 1, 3, 4, 5, 31, 64, 1001):
+        s = "".join(rng.choice(list("ACGT"), size=n))
+        assert np.array_equal(dbg.pack_ascii(s), synth.pack_codes(synth.ascii_to_codes(s)))
+
+
+def test_pack_ascii_phase_and_rejection(lib):
+    out = dbg.pack_ascii("GT", phase=2)
+    assert list(out) == [(2 << 4) | (3 << 6)]
+    with pytest.raises(dbg.DbgError) as e:
+        dbg.pack_ascii("ACGNA")
+    assert e.value.code == dbg.ERR_INVALID_ARG and "at 3" in str(e.value)
+
+
+def test_argument_errors_return_before_any_launch(lib):
+    h = ctypes.c_void_p()
+    assert lib.dbg_create(1, 10, ctypes.byref(h)) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_create(33, 10, ctypes.byref(h)) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_create(21, 0, ctypes.byref(h)) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_create(21, 10, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_insert_reads(None, None, None, 5, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_insert_reads_host(None, None, None, 5, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_insert_batch(None, 3, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_insert_batch(None, 0, None) == dbg.OK
+    assert lib.dbg_get_status(None, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_stats(None, None, None, None) == dbg.ERR_INVALID_ARG
+    n = ctypes.c_uint64()
+    assert lib.dbg_export_sorted(None, None, None, 0, ctypes.byref(n), None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_probe_random_sectors(None, 1, 1, 0, 0, None) == dbg.ERR_INVALID_ARG
+    lib.dbg_destroy(None)
+
+
+def test_create_fails_loudly_without_a_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(dbg.DbgError) as e:
+        dbg.Graph(21, 1000)
+    assert e.value.code in (dbg.ERR_CUDA, dbg.ERR_OOM)
