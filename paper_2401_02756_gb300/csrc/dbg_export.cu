@@ -41,8 +41,10 @@ __global__ void k_compact(const Slot *t, uint64_t n_slots, unsigned long long *k
 __global__ void k_gather(const Slot *t, const unsigned long long *idx, uint4 *counts, uint64_t n) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint4 *c = reinterpret_cast<const uint4 *>(&t[idx[i]].cnt[0]);
-    counts[i] = *c;
+    // the counters sit at byte 8 of the slot: 8-byte aligned, not 16
+    const uint2 *c = reinterpret_cast<const uint2 *>(&t[idx[i]].cnt[0]);
+    const uint2 lo = c[0], hi = c[1];
+    counts[i] = make_uint4(lo.x, lo.y, hi.x, hi.y);
   }
 }
 

@@ -1,0 +1,55 @@
+"""Full-size parity: the benchmark workloads built on the GPU in the launch
+configuration the benchmark times (default tuning, table of 1.5x the
+distinct vertices) must reproduce, bit for bit, the oracle's graph as
+recorded by tests/golden/make_golden.py (vertex and edge totals and the
+SHA-256 of every oracle shard of the sorted export)."""
+
+import hashlib
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import to_device
+from paper_2401_02756_gb300 import build, dbg, synth
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "workload_digests.json")
+
+
+def digest(keys, counts):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(keys, dtype="<u8").tobytes())
+    h.update(np.ascontiguousarray(counts, dtype="<u4").tobytes())
+    return h.hexdigest()
+
+
+@pytest.mark.parametrize("name", ["10kb_k21", "5mbp_50x_k31", "100mbp_30x_k31"])
+def test_full_size_workload_matches_oracle_digests(name):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    gold = json.load(open(GOLD)).get(name) if os.path.exists(GOLD) else None
+    if gold is None:
+        pytest.skip(f"no recorded oracle digest for {name}")
+    build.build()
+    rs = synth.WORKLOADS[name]()
+    assert rs.n_edges() == gold["n_edges"] and rs.n_reads == gold["n_reads"]
+    g = dbg.Graph(rs.k, int(math.ceil(1.5 * gold["n_vertices"])))
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    del packed, offsets
+    assert g.status() == dbg.OK
+    assert g.stats() == (gold["n_vertices"], gold["n_edges"])
+    keys, counts = g.export()
+    g.close()
+    P = gold["shard_mod"]
+    sh = oracle.shard_of_keys(keys, rs.k, P) if P > 1 else np.zeros(keys.size, np.uint64)
+    for p in range(P):
+        sel = sh == p
+        assert int(sel.sum()) == gold["shards"][p]["n_vertices"], p
+        assert digest(keys[sel], counts[sel]) == gold["shards"][p]["sha256"], p
