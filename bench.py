@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--probe-sweep", action="store_true",
+                    help="print the random-sector probe rate over buffer sizes and exit")
     return ap.parse_args()
 
 
@@ -406,9 +408,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_probe_sweep():
+    """Random 32-byte-sector probe (K5) rate over buffer sizes, one JSON line each."""
+    import torch
+
+    from paper_2401_02756_gb300 import build as _build
+    from paper_2401_02756_gb300 import dbg
+    _build.build()
+    dbg.load()
+    n_ops = 1 << 30
+    for n_slots in [1 << 18, 1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24, 1 << 26, 1 << 28, 633846003]:
+        buf = torch.zeros(n_slots * 32, dtype=torch.uint8, device="cuda")
+        for mode in (0, 1, 2):
+            dbg.probe_random_sectors(buf, n_slots, 1 << 26, 3, mode, None)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dbg.probe_random_sectors(buf, n_slots, n_ops, 5 + mode, mode, None)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            print(json.dumps({"n_slots": n_slots, "MB": n_slots * 32 / 2 ** 20, "mode": mode,
+                              "ms": ms, "Gops": n_ops / ms / 1e6}), flush=True)
+        del buf
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.probe_sweep:
+        run_probe_sweep()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
