@@ -50,7 +50,8 @@ typedef enum dbg_status {
   DBG_ERR_CAPACITY = 3,         /* sticky: a vertex found no free slot within max_probes */
   DBG_ERR_CUDA = 4,             /* a CUDA runtime call failed (see dbg_last_cuda_error) */
   DBG_ERR_BUFFER_TOO_SMALL = 5, /* export: max_n < number of vertices (n_out tells how many) */
-  DBG_ERR_BAD_OFFSETS = 6       /* sticky: the GPU saw offsets[r+1] < offsets[r] */
+  DBG_ERR_BAD_OFFSETS = 6,      /* sticky: the GPU saw offsets[r+1] < offsets[r] */
+  DBG_ERR_NOALLOC_LIMIT = 7     /* dbg_export_sorted_noalloc: graph larger than its fixed scratch */
 } dbg_status;
 
 typedef struct dbg_graph *dbg_handle;
@@ -161,6 +162,34 @@ int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *strea
  * status (nothing exported when it is set). */
 int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, uint64_t max_n,
                       uint64_t *n_out, void *stream);
+
+/* Fixed scratch of dbg_export_sorted_noalloc, and the largest graph it exports. */
+#define DBG_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define DBG_NOALLOC_EXPORT_MAX_VERTICES (1u << 19)
+
+/* dbg_export_sorted without any device allocation.  The paper has no
+ * counterpart: this exists for callers that must not allocate device memory
+ * while they run -- a serving loop held to a memory budget that another
+ * component accounts for, a framework that owns every device allocation, or
+ * code that cannot accept the device-wide synchronisation cudaMalloc/cudaFree
+ * may cause.  Same result and ordering as dbg_export_sorted, but:
+ *   - keys_out (uint64 [n]) and counts_out (uint32 [n][4]) are DEVICE
+ *     pointers owned by the caller, both required;
+ *   - its temporary memory is a fixed DBG_NOALLOC_SCRATCH_BYTES device array
+ *     inside libdbg.so, held by every GPU that loads the library until the
+ *     process exits, so a graph of more than DBG_NOALLOC_EXPORT_MAX_VERTICES
+ *     vertices is refused with DBG_ERR_NOALLOC_LIMIT (*n_out still receives
+ *     the vertex count);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture;
+ *   - every call on a device shares the one array: calls whose GPU work
+ *     overlaps (different streams, or host threads) race and must be
+ *     serialised by the caller.
+ * Waits for `stream`.  Errors: INVALID_ARG, CUDA, BUFFER_TOO_SMALL (max_n <
+ * vertices), NOALLOC_LIMIT, and the sticky status. */
+int dbg_export_sorted_noalloc(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out,
+                              uint64_t max_n, uint64_t *n_out, void *stream);
 
 /* Host helper: pack n ASCII bases (A, C, G, T; upper case) into out, which
  * holds ceil(n/4) bytes, starting at base position `phase` (0..3) of out[0]

@@ -445,6 +445,7 @@ extern "C" const char *dbg_strerror(int code) {
     case DBG_ERR_CUDA: return "CUDA error";
     case DBG_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
     case DBG_ERR_BAD_OFFSETS: return "offsets are not non-decreasing";
+    case DBG_ERR_NOALLOC_LIMIT: return "graph larger than the no-alloc export's fixed scratch";
     default: return "unknown status";
   }
 }

@@ -18,14 +18,17 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdbg.so")
 
-OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_BUFFER_TOO_SMALL, ERR_BAD_OFFSETS = range(7)
+(OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_BUFFER_TOO_SMALL, ERR_BAD_OFFSETS,
+ ERR_NOALLOC_LIMIT) = range(8)
 STATUS_NAMES = {0: "DBG_OK", 1: "DBG_ERR_INVALID_ARG", 2: "DBG_ERR_OOM", 3: "DBG_ERR_CAPACITY",
-                4: "DBG_ERR_CUDA", 5: "DBG_ERR_BUFFER_TOO_SMALL", 6: "DBG_ERR_BAD_OFFSETS"}
+                4: "DBG_ERR_CUDA", 5: "DBG_ERR_BUFFER_TOO_SMALL", 6: "DBG_ERR_BAD_OFFSETS",
+                7: "DBG_ERR_NOALLOC_LIMIT"}
+NOALLOC_EXPORT_MAX_VERTICES = 1 << 19
 
 EXPORTED = [
     "dbg_create", "dbg_create_ex", "dbg_destroy", "dbg_reset", "dbg_set_tuning", "dbg_get_info",
     "dbg_insert_reads", "dbg_insert_reads_host", "dbg_insert_batch", "dbg_get_status", "dbg_stats",
-    "dbg_export_sorted", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
+    "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
     "dbg_probe_random_sectors",
 ]
 
@@ -80,6 +83,7 @@ def load() -> ctypes.CDLL:
         "dbg_get_status": (I, [P, P]),
         "dbg_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
         "dbg_export_sorted": (I, [P, P, P, U64, ctypes.POINTER(U64), P]),
+        "dbg_export_sorted_noalloc": (I, [P, P, P, U64, ctypes.POINTER(U64), P]),
         "dbg_pack_ascii": (I, [ctypes.c_char_p, U64, P, I, ctypes.POINTER(U64)]),
         "dbg_strerror": (ctypes.c_char_p, [I]),
         "dbg_last_cuda_error": (ctypes.c_char_p, []),
