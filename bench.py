@@ -44,10 +44,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="100mbp_30x_k31")
+    ap.add_argument("--workload", default="100mbp_30x_k31",
+                    help="100mbp_30x_k31 | 5mbp_50x_k31 | 10kb_k21 | batch256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="insert launch shape, e.g. apply_unroll=4,insert_path=2 (graph unchanged)")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="print the random-sector probe rate over buffer sizes and exit")
     return ap.parse_args()
@@ -77,19 +80,19 @@ def measured_peaks():
 
 def kernel_source_digest():
     h = hashlib.sha256()
-    for f in ("dbg_insert.cu", "dbg_internal.cuh"):
+    for f in ("dbg_insert.cu", "dbg_binned.cu", "dbg_binned.cuh", "dbg_tiles.cuh", "dbg_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2401_02756_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per insert launch from a committed ncu summary, if it was
-    taken on the current kernel source."""
+def recorded_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it
+    was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "insert_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(workload)
+    e = d.get(workload, {}).get(kernel)
     if not e or e.get("kernel_source_digest") != kernel_source_digest():
         return None
     return e.get("dram_bytes_per_launch")
@@ -222,6 +225,9 @@ def run_ours(args):
         pilot.close()
     capacity = int(math.ceil(1.5 * D))
     g = dbg.Graph(rs.k, capacity)
+    tuning = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.tuning.split(",") if kv}
+    if tuning:
+        g.set_tuning(**tuning)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -239,6 +245,7 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.enable_kernel_timing(K)  # per-kernel CUDA events inside each insert call, same stream
     clocks = ClockSampler(dev)
     if dist:
         dist.barrier()
@@ -261,6 +268,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     k1_ms = [b.elapsed_time(c) for a, b, c in ev]
     k2_ms = [a.elapsed_time(b) for a, b, c in ev]
+    kt = g.kernel_times(K)
+    g.enable_kernel_timing(0)
     if dist:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -271,10 +280,33 @@ def run_ours(args):
 
     value = edges * K * world / (total_ms / 1e3)
     k1_mean_s = statistics.mean(k1_ms) / 1e3
-    alg_bytes = touches * SECTOR_RMW_BYTES + rs.packed.nbytes + rs.offsets.nbytes
+    in_bytes = rs.packed.nbytes + rs.offsets.nbytes
+    # algorithmic bytes per launch of each kernel
+    kernel_bytes = {
+        "direct": touches * SECTOR_RMW_BYTES + in_bytes,
+        "bin_count": in_bytes,
+        "bin_scan": 0,
+        "bin_scatter": in_bytes + 8 * touches,
+        "bin_apply": 8 * touches + SECTOR_RMW_BYTES * D,
+        "direct_fallback": 0,
+    }
+    names = dbg.Graph.KERNELS
+    kernels = {}
+    for j, name in enumerate(names):
+        col = [float(x) for x in kt[:, j] if x >= 0]
+        if col:
+            kernels[name] = {"ms": statistics.mean(col), "launches_per_step": 1}
+    launched = sum(1 for j in range(len(names)) if (kt[:, j] >= 0).any())
+    dom = max(kernels, key=lambda n: kernels[n]["ms"])
+    dom_s = kernels[dom]["ms"] / 1e3
+    alg_bytes = kernel_bytes[dom]
     peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / k1_mean_s / 1e9
-    traffic = recorded_traffic(args.workload)
+    achieved = alg_bytes / dom_s / 1e9
+    traffic = recorded_traffic(args.workload, dom)
+    for name in kernels:
+        b = kernel_bytes[name]
+        kernels[name]["alg_gb"] = b / 1e9
+        kernels[name]["gbs"] = b / (kernels[name]["ms"] / 1e3) / 1e9 if b else None
 
     # measured random-sector ceiling (K5) over a buffer the size of the table
     probe = None
@@ -295,7 +327,7 @@ def run_ours(args):
         probe = {"touches": touches, "red_only_ms": round(ms[0], 3), "load_red_ms": round(ms[1], 3),
                  "load_red_touches_per_s": touches / (ms[1] / 1e3),
                  "load_red_gbs_equiv": touches * SECTOR_RMW_BYTES / (ms[1] / 1e3) / 1e9,
-                 "insert_frac_of_probe": (ms[1] / 1e3) / k1_mean_s}
+                 "insert_rate_over_probe_rate": (ms[1] / 1e3) / k1_mean_s}
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -344,20 +376,22 @@ def run_ours(args):
                        "distinct_vertices": D, "distinct_source": d_source,
                        "capacity_slots": capacity, "table_gb": capacity * 32 / 1e9,
                        "l2": "table and reads larger than L2 (no flush needed)",
+                       "tuning": tuning or "default",
                        "parallelism": f"replicas x{world}"},
             "insert_only_edges_per_s": edges / k1_mean_s,
-            "k1_insert_ms": {"mean": statistics.mean(k1_ms), "min": min(k1_ms), "max": max(k1_ms)},
+            "insert_ms": {"mean": statistics.mean(k1_ms), "min": min(k1_ms), "max": max(k1_ms)},
+            "insert_path": "binned" if "bin_apply" in kernels else "direct",
+            "kernels": kernels,
             "k2_init_ms": statistics.mean(k2_ms),
             "step_ms_p50": float(np.percentile(step_ms, 50)),
             "step_ms_p99": float(np.percentile(step_ms, 99)),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
-                         "alg_bytes_per_launch": alg_bytes,
-                         "alg_bytes_per_edge": alg_bytes / edges},
+                         "alg_bytes_per_launch": alg_bytes},
             "random_sector_probe": probe,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
-            "gpu_launches": 2 * K,
+            "gpu_launches": (1 + launched) * K,
             "kernel_source_digest": kernel_source_digest(),
         }
         print(json.dumps(line), flush=True)
@@ -408,6 +442,83 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """256 independent samples: one batched insert (dbg_insert_batch) against
+    one plain dbg_insert_reads per sample, both into freshly emptied tables
+    of 1.5x each sample's distinct vertices (counted by a pilot build)."""
+    import torch
+
+    from paper_2401_02756_gb300 import build as _build
+    from paper_2401_02756_gb300 import dbg, synth
+    _build.build()
+    dbg.load()
+    torch.cuda.set_device(0)
+    t_gen = time.perf_counter()
+    samples = synth.batch_samples(256, seed=4)
+    t_gen = time.perf_counter() - t_gen
+    dev_in, graphs, edges = [], [], 0
+    for rs in samples:
+        pk = torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda()
+        of = torch.from_numpy(rs.offsets.view(np.int64).copy()).cuda()
+        touches = int(np.maximum(rs.lengths() - rs.k + 2, 0).sum())
+        pilot = dbg.Graph(rs.k, touches + 64)
+        pilot.set_tuning(insert_path=1)
+        pilot.insert(pk, of)
+        D, _ = pilot.stats()
+        pilot.close()
+        g = dbg.Graph(rs.k, int(math.ceil(1.5 * D)) + 64)
+        dev_in.append((pk, of))
+        graphs.append(g)
+        edges += rs.n_edges()
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def reset_all():
+        for g in graphs:
+            g.reset(stream)
+
+    def batched():
+        dbg.insert_batch([(g, pk, of) for g, (pk, of) in zip(graphs, dev_in)], stream)
+
+    def plain():
+        for g, (pk, of) in zip(graphs, dev_in):
+            g.insert(pk, of, stream=stream)
+
+    results = {}
+    for name, fn in (("batched", batched), ("per_sample", plain)):
+        for _ in range(args.warmup):
+            reset_all()
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            reset_all()
+            a, b = ev(), ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        results[name] = ms
+        for g in graphs:
+            if g.status() != dbg.OK:
+                raise RuntimeError(f"{name}: build failed")
+    bm, pm = statistics.mean(results["batched"]), statistics.mean(results["per_sample"])
+    line = {
+        "metric": METRIC, "value": edges / (bm / 1e3), "unit": "edges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": bm, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batch256", "samples": len(samples), "edges": edges,
+                   "k": sorted({rs.k for rs in samples}), "generation_s": t_gen},
+        "per_sample_edges_per_s": edges / (pm / 1e3),
+        "batched_over_per_sample": pm / bm,
+        "batch_ms_p50": float(np.percentile(results["batched"], 50)),
+        "batch_ms_p99": float(np.percentile(results["batched"], 99)),
+    }
+    for g in graphs:
+        g.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_probe_sweep():
     """Random 32-byte-sector probe (K5) rate over buffer sizes, one JSON line each."""
     import torch
@@ -438,6 +549,8 @@ def main():
     args = parse_args()
     if args.probe_sweep:
         run_probe_sweep()
+    elif args.workload == "batch256" and args.impl == "ours":
+        run_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -63,6 +63,9 @@ typedef struct dbg_tuning {
   int tile_reads;     /* reads staged per tile, in [1, block_threads] (default block_threads) */
   int grid_ctas;      /* CTAs in the persistent grid (default: SMs x resident CTAs per SM) */
   int warp_aggregate; /* 1: merge equal keys of a warp with __match_any_sync; 0: off; -1: default */
+  int insert_path;    /* 0: automatic; 1: direct; 2: binned (k <= 31; see dbg_insert_reads) */
+  int apply_unroll;   /* binned apply: events in flight per thread, 4, 8 or 16 (0: default 4) */
+  int apply_counters; /* binned apply: work counters the warps draw chunks from, 1..64 (0: 16) */
 } dbg_tuning;
 
 typedef struct dbg_info {
@@ -71,6 +74,7 @@ typedef struct dbg_info {
   uint64_t table_bytes; /* device bytes held by the table */
   uint32_t max_probes;  /* slots probed per vertex before DBG_ERR_CAPACITY */
   int device;           /* CUDA device the table lives on */
+  uint64_t event_capacity; /* binned-insert event buffer, in events (0: not allocated) */
 } dbg_info;
 
 /* Create an empty graph for k-mers of length k (2..32) with room for
@@ -99,6 +103,24 @@ int dbg_reset(dbg_handle h, void *stream);
  * Errors: INVALID_ARG for out-of-range fields. */
 int dbg_set_tuning(dbg_handle h, const dbg_tuning *t);
 
+/* Size the binned insert's event buffer for `events` vertex positions per call
+ * (8 bytes each; 0 = the default of 4 per table slot), allocating it now.
+ * Synchronizes the device if the buffer grows.  Errors: INVALID_ARG, OOM. */
+int dbg_reserve_events(dbg_handle h, uint64_t events);
+
+/* Measurement aid: record CUDA events around every kernel of the next insert
+ * calls on this handle (dbg_insert_reads / dbg_insert_reads_host), keeping
+ * the last `calls` calls (0 turns it off).  Synchronizes the device. */
+int dbg_enable_kernel_timing(dbg_handle h, int calls);
+
+/* Kernel durations of the kept calls, oldest first: out_ms[6*c + j] for
+ * kernel j = 0 direct insert, 1 bin count, 2 bin scan, 3 bin scatter, 4 bin
+ * apply, 5 direct insert run as the binned fall-back (it returns at once when
+ * the binned kernels did the work);
+ * -1 for a kernel the call did not launch.  Waits for the recorded events.
+ * *n_calls receives the number of calls written (at most max_calls). */
+int dbg_kernel_times(dbg_handle h, float *out_ms, int max_calls, int *n_calls);
+
 /* Fill *out with the handle's parameters. */
 int dbg_get_info(dbg_handle h, dbg_info *out);
 
@@ -106,20 +128,34 @@ int dbg_get_info(dbg_handle h, dbg_info *out);
  * the addRightVertex prose): for each length-k substring, find or claim the
  * prefix vertex and count the label s_{k-1}, and find or claim the suffix
  * vertex.  `packed` and `offsets` are DEVICE pointers (see the conventions
- * above); one kernel is launched on `stream`.  Calls on one handle may be
+ * above); the work is launched on `stream`.  Calls on one handle may be
  * issued from several streams at once: counts add, so the graph does not
- * depend on the order.  n_reads == 0 launches nothing.
- * Errors: INVALID_ARG (NULL handle, NULL pointer with n_reads > 0), CUDA;
- * sticky CAPACITY / BAD_OFFSETS. */
+ * depend on the order (one handle is not safe to use from several host
+ * threads at once).  n_reads == 0 launches nothing.
+ *
+ * Two paths give the same graph.  The direct path is one kernel that updates
+ * the table as it walks the reads.  The binned path (k <= 31) first writes
+ * one 8-byte event per vertex position grouped by table region, then applies
+ * the events region by region so the table lines being updated stay in L2;
+ * it is chosen automatically for tables of 256 MiB or more and needs an event
+ * buffer owned by the handle (default 4 events per slot, allocated by the
+ * first call that needs it, or sized with dbg_reserve_events).  A call with
+ * more vertex positions than the buffer holds runs the direct kernel instead
+ * (decided on the device).  Binned calls on one handle run one after another.
+ * Errors: INVALID_ARG (NULL handle, NULL pointer with n_reads > 0), OOM (event
+ * buffer), CUDA; sticky CAPACITY / BAD_OFFSETS. */
 int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
                      uint64_t n_reads, void *stream);
 
 /* As dbg_insert_reads, with `packed` and `offsets` in HOST memory (pinned
  * memory gives asynchronous copies; pageable memory works but copies are
  * staged by the driver).  The reads are copied to device staging buffers
- * owned by the handle in chunks, each chunk's copy overlapping the previous
- * chunk's insert.  Returns after the last chunk has been launched; the host
- * buffers may be reused once `stream` has passed the call.
+ * owned by the handle: whole, when packed bytes plus offsets take at most
+ * 4 GiB, and inserted with one call; otherwise in chunks of at most 2^22
+ * reads / 256 MiB, each chunk's copy overlapping the previous chunk's insert.
+ * The offsets are validated on the host first (INVALID_ARG if one decreases).
+ * Returns after the last insert has been launched; the host buffers may be
+ * reused once `stream` has passed the call.
  * Errors: as dbg_insert_reads, plus OOM for the staging buffers. */
 int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
                           uint64_t n_reads, void *stream);

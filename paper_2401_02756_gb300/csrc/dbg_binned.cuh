@@ -1,0 +1,42 @@
+// Binned insert (see dbg_binned.cu): geometry and the host entry.
+#pragma once
+
+#include "dbg_internal.cuh"
+
+namespace dbg {
+
+constexpr int kBinMaxParts = 2048;           // regions of the table, at most
+constexpr uint64_t kBinMinTableBytes = 256ull << 20;  // auto mode: tables at least this big
+constexpr uint64_t kBinMinEvents = 16ull << 20;       // smallest event buffer
+constexpr uint64_t kBinEventsPerSlot = 4;             // default event buffer: 4 events per slot
+
+constexpr uint64_t kBinSlices = 4096;                // count/scatter work units, at most
+constexpr int kBinMinShift = 20;                     // regions of at least 2^20 slots (32 MiB)
+
+constexpr int kBinApplyCounters = 64;                // apply: chunk counters, at most
+
+// meta area: begin[kBinMaxParts + 1] | counts[kBinMaxParts] | cursor[kBinMaxParts] |
+// counters[4] (the last holds the flag) | apply counters[kBinApplyCounters] |
+// slice histograms u32[kBinSlices][kBinMaxParts]
+constexpr size_t kBinMetaBytes =
+    ((size_t)kBinMaxParts + 1) * 8 + 2 * (size_t)kBinMaxParts * 8 + 4 * 8 +
+    (size_t)kBinApplyCounters * 8 + (size_t)kBinSlices * kBinMaxParts * 4;
+
+struct BinGeometry {
+  int shift;  // region = slots [p << shift, (p + 1) << shift)
+  int parts;
+};
+
+BinGeometry bin_geometry(uint64_t n_slots);
+
+// Make sure the handle holds an event buffer of at least `events` events
+// (0: the default size) and the meta area.
+int ensure_bin_scratch(dbg_handle h, uint64_t events);
+
+// Insert one read set through count / scan / scatter / apply, falling back to
+// the direct kernel on the device when the events do not fit the buffer.
+// `call`: the kernel timer's ring slot for this call (-1: not timed).
+int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
+                  cudaStream_t s, int call);
+
+}  // namespace dbg

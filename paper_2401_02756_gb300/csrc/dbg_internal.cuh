@@ -106,9 +106,31 @@ struct dbg_graph {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+  // binned insert scratch (allocated when a binned insert first needs it)
+  uint64_t *bin_ev = nullptr;               // events, 8 bytes each
+  uint64_t bin_cap = 0;                     // capacity in events
+  unsigned long long *bin_meta = nullptr;   // region counts, ranges, cursors, flag
+  cudaEvent_t bin_done = nullptr;           // orders binned calls that share the scratch
+  // optional per-kernel timing of insert calls (dbg_enable_kernel_timing)
+  int timer_cap = 0;                        // calls kept
+  int timer_calls = 0;                      // calls recorded (may exceed timer_cap)
+  cudaEvent_t *timer_ev = nullptr;          // timer_cap * kTimerMarks events
+  signed char *timer_mark_set = nullptr;    // which marks of each call were recorded
 };
 
 namespace dbg {
+
+// Kernel boundaries of one insert call for the optional timer: mark i is
+// recorded before kernel i; the last mark after the last kernel.
+//   0 direct insert | 1 bin count | 2 bin scan | 3 bin scatter | 4 bin apply |
+//   5 gated direct insert (binned fall-back) | 6 end
+constexpr int kTimerMarks = 7;
+constexpr int kTimerKernels = kTimerMarks - 1;
+
+// Start recording a call (no-op when timing is off); returns the ring slot.
+int timer_begin_call(dbg_handle h);
+// Record mark `m` of ring slot `call` on stream s (no-op when call < 0).
+void timer_mark(dbg_handle h, int call, int m, cudaStream_t s);
 
 // Error plumbing shared by the entry points (host side).
 int cuda_fail(cudaError_t e, const char *what);
@@ -136,8 +158,11 @@ struct ItemPack {
 
 // Launch the insert kernel over host-side descriptors items[0..n_items)
 // (tile_begin already set, total_tiles their sum); n_items <= kBatchItems.
+// `gate`: if not null, the kernel does nothing when *gate != 0 (read on the
+// device when it runs).
 int launch_insert(const ItemDesc *items, int n_items, uint64_t total_tiles,
-                  const dbg_tuning &tuning, int sm_count, cudaStream_t stream);
+                  const dbg_tuning &tuning, int sm_count, cudaStream_t stream,
+                  const uint32_t *gate = nullptr);
 
 // Resolved tuning (defaults filled in).
 dbg_tuning resolve_tuning(const dbg_tuning &t);

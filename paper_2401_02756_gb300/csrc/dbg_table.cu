@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "dbg_binned.cuh"
 #include "dbg_internal.cuh"
 
 namespace dbg {
@@ -97,6 +98,35 @@ int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, c
   return DBG_OK;
 }
 
+static void timer_free(dbg_handle h) {
+  if (h->timer_ev) {
+    for (int i = 0; i < h->timer_cap * kTimerMarks; ++i)
+      if (h->timer_ev[i]) cudaEventDestroy(h->timer_ev[i]);
+  }
+  delete[] h->timer_ev;
+  delete[] h->timer_mark_set;
+  h->timer_ev = nullptr;
+  h->timer_mark_set = nullptr;
+  h->timer_cap = 0;
+  h->timer_calls = 0;
+}
+
+int timer_begin_call(dbg_handle h) {
+  if (h->timer_cap <= 0) return -1;
+  const int call = h->timer_calls % h->timer_cap;
+  h->timer_calls += 1;
+  for (int m = 0; m < kTimerMarks; ++m) h->timer_mark_set[call * kTimerMarks + m] = 0;
+  return call;
+}
+
+void timer_mark(dbg_handle h, int call, int m, cudaStream_t s) {
+  if (call < 0 || h->timer_cap <= 0) return;
+  if (cudaEventRecord(h->timer_ev[call * kTimerMarks + m], s) == cudaSuccess)
+    h->timer_mark_set[call * kTimerMarks + m] = 1;
+}
+
+void destroy_timer(dbg_handle h) { timer_free(h); }
+
 ItemDesc make_item(dbg_handle h, const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads,
                    uint64_t origin) {
   ItemDesc it{};
@@ -185,6 +215,10 @@ extern "C" void dbg_destroy(dbg_handle h) {
     if (h->ev_consumed[i]) cudaEventDestroy(h->ev_consumed[i]);
   }
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  cudaFree(h->bin_ev);
+  cudaFree(h->bin_meta);
+  if (h->bin_done) cudaEventDestroy(h->bin_done);
+  dbg::destroy_timer(h);
   delete h;
 }
 
@@ -213,6 +247,10 @@ extern "C" int dbg_set_tuning(dbg_handle h, const dbg_tuning *t) {
   if (r.tile_reads < 0 || r.tile_reads > bt) return DBG_ERR_INVALID_ARG;
   if (r.grid_ctas < 0) return DBG_ERR_INVALID_ARG;
   if (r.warp_aggregate < -1 || r.warp_aggregate > 1) return DBG_ERR_INVALID_ARG;
+  if (r.insert_path < 0 || r.insert_path > 2) return DBG_ERR_INVALID_ARG;
+  if (r.apply_unroll != 0 && r.apply_unroll != 4 && r.apply_unroll != 8 && r.apply_unroll != 16)
+    return DBG_ERR_INVALID_ARG;
+  if (r.apply_counters < 0 || r.apply_counters > 64) return DBG_ERR_INVALID_ARG;
   h->tuning = r;
   return DBG_OK;
 }
@@ -224,8 +262,93 @@ extern "C" int dbg_get_info(dbg_handle h, dbg_info *out) {
   out->table_bytes = h->n_slots * sizeof(dbg::Slot);
   out->max_probes = h->max_probes;
   out->device = h->device;
+  out->event_capacity = h->bin_cap;
   return DBG_OK;
 }
+
+extern "C" int dbg_enable_kernel_timing(dbg_handle h, int calls) {
+  if (!h || calls < 0) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  DBG_CK(cudaDeviceSynchronize());
+  dbg::destroy_timer(h);
+  if (calls == 0) return DBG_OK;
+  h->timer_ev = new (std::nothrow) cudaEvent_t[(size_t)calls * dbg::kTimerMarks]();
+  h->timer_mark_set = new (std::nothrow) signed char[(size_t)calls * dbg::kTimerMarks]();
+  if (!h->timer_ev || !h->timer_mark_set) {
+    dbg::destroy_timer(h);
+    return DBG_ERR_OOM;
+  }
+  h->timer_cap = calls;
+  for (int i = 0; i < calls * dbg::kTimerMarks; ++i) {
+    cudaError_t e = cudaEventCreate(&h->timer_ev[i]);
+    if (e != cudaSuccess) {
+      dbg::destroy_timer(h);
+      return dbg::cuda_fail(e, "cudaEventCreate(timer)");
+    }
+  }
+  return DBG_OK;
+}
+
+extern "C" int dbg_kernel_times(dbg_handle h, float *out_ms, int max_calls, int *n_calls) {
+  if (!h || !n_calls || max_calls < 0 || (max_calls > 0 && !out_ms)) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  const int kept = std::min(h->timer_calls, h->timer_cap);
+  const int first = h->timer_calls - kept;  // oldest kept call
+  const int n = std::min(kept, max_calls);
+  for (int c = 0; c < n; ++c) {
+    const int slot = (first + c) % h->timer_cap;
+    const cudaEvent_t *ev = h->timer_ev + (size_t)slot * dbg::kTimerMarks;
+    const signed char *set = h->timer_mark_set + (size_t)slot * dbg::kTimerMarks;
+    for (int kk = 0; kk < dbg::kTimerKernels; ++kk) {
+      float ms = -1.0f;
+      // kernel kk spans mark kk to the next recorded mark
+      if (set[kk]) {
+        int nx = kk + 1;
+        while (nx < dbg::kTimerMarks && !set[nx]) ++nx;
+        if (nx < dbg::kTimerMarks) {
+          DBG_CK(cudaEventSynchronize(ev[nx]));
+          DBG_CK(cudaEventElapsedTime(&ms, ev[kk], ev[nx]));
+        }
+      }
+      out_ms[(size_t)c * dbg::kTimerKernels + kk] = ms;
+    }
+  }
+  *n_calls = n;
+  return DBG_OK;
+}
+
+extern "C" int dbg_reserve_events(dbg_handle h, uint64_t events) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  return dbg::ensure_bin_scratch(h, events);
+}
+
+namespace {
+
+// Path for one read set into h: binned when asked for, or automatically for
+// large tables; never for k = 32 (keys of 62 bits do not fit an event).
+bool want_binned(dbg_handle h) {
+  if (h->k > 31) return false;
+  const int path = h->tuning.insert_path;
+  if (path == 1) return false;
+  if (path == 2) return true;
+  return h->n_slots * sizeof(dbg::Slot) >= dbg::kBinMinTableBytes;
+}
+
+int insert_one(dbg_handle h, const dbg::ItemDesc &it, uint64_t tiles, cudaStream_t s) {
+  const int call = dbg::timer_begin_call(h);
+  if (want_binned(h) && (h->bin_cap > 0 || dbg::ensure_bin_scratch(h, 0) == DBG_OK))
+    return dbg::launch_binned(h, it, tiles, h->tuning, s, call);
+  dbg::timer_mark(h, call, 0, s);
+  const int st = dbg::launch_insert(&it, 1, tiles, h->tuning, h->sm_count, s);
+  dbg::timer_mark(h, call, 1, s);  // direct call: kernel 0 spans marks 0..1
+  return st;
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // inserts
@@ -241,14 +364,14 @@ extern "C" int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint6
   const dbg_tuning t = dbg::resolve_tuning(h->tuning);
   const uint64_t tiles = (n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
   const dbg::ItemDesc it = dbg::make_item(h, packed, offsets, n_reads, 0);
-  return dbg::launch_insert(&it, 1, tiles, h->tuning, h->sm_count,
-                            static_cast<cudaStream_t>(stream));
+  return insert_one(h, it, tiles, static_cast<cudaStream_t>(stream));
 }
 
 namespace {
 
-constexpr uint64_t kStageBytes = 64ull << 20;   // packed bytes per host chunk
-constexpr uint64_t kStageReads = 1ull << 20;    // reads per host chunk
+constexpr uint64_t kStageAllBytes = 4ull << 30;  // inputs up to this size are staged whole
+constexpr uint64_t kStageBytes = 256ull << 20;   // otherwise: packed bytes per host chunk
+constexpr uint64_t kStageReads = 1ull << 22;     // otherwise: reads per host chunk
 
 int grow_stage(dbg_handle h, uint64_t bytes, uint64_t reads) {
   if (bytes > h->stage_packed_bytes) {
@@ -295,10 +418,18 @@ extern "C" int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const dbg_tuning t = dbg::resolve_tuning(h->tuning);
 
-  // chunk boundaries: at most kStageReads reads and about kStageBytes bytes
+  // chunk boundaries: the whole input when it is small enough (one insert,
+  // which the binned path needs to see the whole read set at once), else at
+  // most kStageReads reads and about kStageBytes bytes per chunk
   std::vector<uint64_t> cuts{0};
   uint64_t max_bytes = 0, max_reads = 0;
-  for (uint64_t r0 = 0; r0 < n_reads;) {
+  const uint64_t all_bytes = ((offsets[n_reads] + 3) >> 2) - (offsets[0] >> 2);
+  if (all_bytes + (n_reads + 1) * sizeof(uint64_t) <= kStageAllBytes) {
+    cuts.push_back(n_reads);
+    max_bytes = all_bytes;
+    max_reads = n_reads;
+  }
+  for (uint64_t r0 = 0; cuts.back() != n_reads && r0 < n_reads;) {
     const uint64_t b0 = offsets[r0] >> 2;
     uint64_t r1 = std::min(n_reads, r0 + kStageReads);
     // shrink until the chunk's bytes fit (always keep at least one read)
@@ -335,7 +466,7 @@ extern "C" int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const 
     const dbg::ItemDesc it =
         dbg::make_item(h, h->stage_packed[b], h->stage_offsets[b], r1 - r0, byte0 * 4);
     const uint64_t tiles = (r1 - r0 + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
-    st = dbg::launch_insert(&it, 1, tiles, h->tuning, h->sm_count, s);
+    st = insert_one(h, it, tiles, s);
     if (st != DBG_OK) return st;
     DBG_CK(cudaEventRecord(h->ev_consumed[b], s));
   }

@@ -1,0 +1,292 @@
+// Read-tile machinery shared by the insert kernels: walk read tiles, stage
+// them in shared memory, and hand every vertex position to a visitor.
+//
+// Work unit: a tile of `tile_reads` consecutive reads of one item.  A CTA
+//   1. stages the tile's offsets in shared memory, computes each read's vertex
+//      count (len - k + 2 for len >= k, else 0: the last vertex of a read is a
+//      target only, Alg. 2 with the addRightVertex prose) and a block-wide
+//      prefix sum of them;
+//   2. stages the packed bases the tile spans in a shared-memory window with
+//      coalesced 16-byte loads (a tile wider than the window is cut into
+//      sub-tiles; a single read wider than the window reads its bases from
+//      global memory);
+//   3. maps each thread to a run of R consecutive vertex positions of the
+//      flattened (sub-)tile; the first key of a run (or of a read inside it)
+//      is extracted -- the k-1 bases, first base most significant -- from two
+//      64-bit window words with a funnel shift and a 2-bit-group reversal,
+//      and the next ones roll: key' = ((key << 2) | label) & mask, where the
+//      label s_{k-1} of one position is the last base of the next key;
+//   4. calls vis.vertex(...) for every position, in block-uniform rounds of
+//      BLOCK * R positions, and vis.round_end() after every round.
+// A visitor whose rounds contain __syncthreads sets kUniformRounds; the
+// insert visitor instead may stop a thread early (vis.stop()).  The CTA walks
+// tiles t_first, t_first + t_stride, ... below t_end; every thread of the CTA
+// must call for_each_vertex with the same arguments.
+#pragma once
+
+#include "dbg_internal.cuh"
+
+namespace dbg {
+
+constexpr int kWinWords = 2048;  // 16 KB window of packed bases per CTA (64 Ki bases)
+constexpr unsigned kFull = 0xffffffffu;
+
+// Dynamic shared memory the tile machinery uses (the visitor's own region
+// follows it, 16-byte aligned).
+__host__ __device__ constexpr size_t tile_smem_bytes(int tile_reads) {
+  return (size_t)(kWinWords + 2) * 8 + (size_t)(tile_reads + 1) * 16;
+}
+
+// What a visitor learns about the item a vertex belongs to.
+struct VertexCtx {
+  Slot *table;
+  uint64_t n_slots;
+  uint32_t *status;
+  uint32_t max_probes;
+  int k;
+  int item;
+};
+
+__device__ __forceinline__ uint4 ldg_stream_v4(const uint8_t *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Key (and label) of the vertex at base p, read from global memory: used only
+// for a read wider than the shared-memory window.
+__device__ __forceinline__ uint64_t key_from_global(const uint8_t *packed, uint64_t nbytes,
+                                                    uint64_t p, int m, uint32_t &label) {
+  const uint64_t b0 = p >> 2;
+  uint64_t lo = 0, hi = 0;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint64_t b = b0 + i;
+    const uint64_t x = b < nbytes ? (uint64_t)__ldg(packed + b) : 0ull;
+    if (i < 8)
+      lo |= x << (8 * i);
+    else
+      hi |= x << (8 * (i - 8));
+  }
+  const uint32_t sh = (uint32_t)(p & 3) * 2;
+  const uint32_t rel = (uint32_t)(p & 3) + (uint32_t)m;  // label base, relative
+  label = (uint32_t)((rel < 32 ? (lo >> (2 * rel)) : (hi >> (2 * rel - 64))) & 3ull);
+  return key_from_words(lo, hi, sh, m);
+}
+
+template <int N>
+__device__ __forceinline__ int find_item(const ItemPack<N> &pk, uint64_t t) {
+  if (N == 1) return 0;
+  int lo = 0, hi = pk.n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pk.d[mid].tile_begin <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Base `pos` of the packed stream from global memory (0 past the end).
+__device__ __forceinline__ uint32_t base_from_global(const uint8_t *packed, uint64_t nbytes,
+                                                     uint64_t pos) {
+  const uint64_t b = pos >> 2;
+  return b < nbytes ? (uint32_t)(__ldg(packed + b) >> (2 * (pos & 3))) & 3u : 0u;
+}
+
+// Walk tiles t_first, t_first + t_stride, ... (< t_end) of the items in `pk`.
+template <int BLOCK, int N, int R, class Visitor>
+__device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_reads,
+                                                unsigned char *smem_raw, Visitor &vis,
+                                                uint64_t t_first, uint64_t t_end,
+                                                uint64_t t_stride) {
+  uint64_t *s_win = reinterpret_cast<uint64_t *>(smem_raw);  // kWinWords + 2
+  uint64_t *s_off = s_win + kWinWords + 2;                     // tile_reads + 1
+  uint64_t *s_vpre = s_off + tile_reads + 1;                   // tile_reads + 1
+
+  __shared__ ItemDesc s_item;
+  __shared__ int s_item_idx;
+  __shared__ uint32_t s_stop;
+  __shared__ uint64_t s_nbytes;
+  __shared__ uint64_t s_warp[BLOCK / 32];
+  __shared__ int s_rb, s_global;
+  __shared__ uint64_t s_wb0;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_item_idx = -1;
+
+  const uint64_t total_tiles = min(pk.total_tiles, t_end);
+  for (uint64_t t = t_first; t < total_tiles; t += t_stride) {
+    if (tid == 0) {
+      const int ii = find_item(pk, t);
+      if (ii != s_item_idx) {
+        s_item = pk.d[ii];
+        s_item_idx = ii;
+        const uint64_t last = s_item.offsets[s_item.n_reads];
+        s_nbytes = last >= s_item.origin ? (last - s_item.origin + 3) >> 2 : 0;
+        if (last < s_item.origin) set_sticky(s_item.status, DBG_ERR_BAD_OFFSETS);
+      }
+      s_stop = ld_volatile_u32(s_item.status);
+    }
+    vis.tile_begin();
+    __syncthreads();
+    if (s_stop == 0u) {
+      const uint8_t *packed = s_item.packed;
+      const uint64_t origin = s_item.origin;
+      const VertexCtx ctx{s_item.table, s_item.n_slots, s_item.status, s_item.max_probes,
+                          s_item.k, s_item_idx};
+      const int k = ctx.k, m = k - 1;
+      const uint64_t nbytes = s_nbytes;
+      const int vec_ok = s_item.vec_ok;
+      const uint64_t r0 = (t - s_item.tile_begin) * (uint64_t)tile_reads;
+      const int nr = (int)min((uint64_t)tile_reads, s_item.n_reads - r0);
+
+      // 1. offsets, vertex counts, exclusive prefix
+      for (int i = tid; i <= nr; i += BLOCK) s_off[i] = s_item.offsets[r0 + i];
+      __syncthreads();
+      uint64_t nv = 0;
+      int bad = 0;
+      if (tid < nr) {
+        const uint64_t a = s_off[tid], b = s_off[tid + 1];
+        if (b < a || a < origin) {
+          bad = 1;
+        } else {
+          const uint64_t len = b - a;
+          nv = len >= (uint64_t)k ? len - (uint64_t)k + 2 : 0;
+        }
+      }
+      bad = __syncthreads_or(bad);
+      if (!bad) {
+        uint64_t incl = nv;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint64_t o = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += o;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+          uint64_t w = lane < BLOCK / 32 ? s_warp[lane] : 0;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t o = __shfl_up_sync(kFull, w, d);
+            if (lane >= d) w += o;
+          }
+          if (lane < BLOCK / 32) s_warp[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const uint64_t excl = incl - nv + (warp > 0 ? s_warp[warp - 1] : 0);
+        if (tid < nr) s_vpre[tid] = excl;
+        if (tid == nr - 1) s_vpre[nr] = excl + nv;
+        __syncthreads();
+
+        // 2-4. sub-tiles whose bases fit the window
+        const uint64_t cap_bytes = (uint64_t)kWinWords * 8 - 16;
+        int ra = 0;
+        while (ra < nr) {
+          if (tid == 0) {
+            const uint64_t wb0 = ((s_off[ra] - origin) >> 2) & ~15ull;
+            auto fits = [&](int rb) {
+              return ((s_off[rb] - origin + 3) >> 2) - wb0 <= cap_bytes;
+            };
+            int rb;
+            if (!fits(ra + 1)) {
+              rb = ra + 1;
+              s_global = 1;
+            } else {
+              int lo = ra + 1, hi = nr;  // largest rb in [lo, hi] that fits
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (fits(mid))
+                  lo = mid;
+                else
+                  hi = mid - 1;
+              }
+              rb = lo;
+              s_global = 0;
+            }
+            s_rb = rb;
+            s_wb0 = wb0;
+          }
+          __syncthreads();
+          const int rb = s_rb;
+          const bool gmode = s_global != 0;
+          const uint64_t wb0 = s_wb0;
+          if (!gmode) {
+            const uint64_t need_end = (s_off[rb] - origin + 3) >> 2;
+            const uint64_t wend = min(need_end, nbytes);
+            const uint64_t nb = wend > wb0 ? wend - wb0 : 0;
+            unsigned char *wbytes = reinterpret_cast<unsigned char *>(s_win);
+            uint64_t done = 0;
+            if (vec_ok) {
+              const uint64_t nvec = nb >> 4;
+              uint4 *wv = reinterpret_cast<uint4 *>(s_win);
+              for (uint64_t i = tid; i < nvec; i += BLOCK) wv[i] = ldg_stream_v4(packed + wb0 + 16 * i);
+              done = nvec << 4;
+            }
+            for (uint64_t i = done + tid; i < nb; i += BLOCK) wbytes[i] = __ldg(packed + wb0 + i);
+            __syncthreads();
+          }
+          const uint64_t v_lo = s_vpre[ra], v_hi = s_vpre[rb];
+          const uint64_t mask = (1ull << (2 * m)) - 1ull;
+          int r = ra;
+          for (uint64_t base = v_lo; base < v_hi; base += (uint64_t)BLOCK * R) {
+            if (!Visitor::kUniformRounds && vis.stop(lane)) break;
+            uint64_t v = base + (uint64_t)tid * R;
+            uint64_t key = kEmpty;
+            uint32_t label = 0;
+            bool have = false;
+#pragma unroll
+            for (int sub = 0; sub < R; ++sub, ++v) {
+              const bool valid = v < v_hi;
+              bool edge = false;
+              if (valid) {
+                bool fresh = !have;
+                while (s_vpre[r + 1] <= v) {
+                  ++r;
+                  fresh = true;
+                }
+                const uint64_t j = v - s_vpre[r];
+                const uint64_t rs = s_off[r];
+                const uint64_t len = s_off[r + 1] - rs;
+                const uint64_t p = rs - origin + j;
+                edge = j + (uint64_t)k <= len;
+                if (!gmode) {
+                  const uint64_t q = p - (wb0 << 2);
+                  if (fresh) {
+                    const uint32_t wi = (uint32_t)(q >> 5);
+                    key = key_from_words(s_win[wi], s_win[wi + 1], (uint32_t)(q & 31) * 2, m);
+                  } else {
+                    key = ((key << 2) | label) & mask;
+                  }
+                  const uint64_t qe = q + (uint64_t)m;
+                  label = (uint32_t)(s_win[qe >> 5] >> ((qe & 31) * 2)) & 3u;
+                } else {
+                  if (fresh) {
+                    key = key_from_global(packed, nbytes, p, m, label);
+                  } else {
+                    key = ((key << 2) | label) & mask;
+                    label = base_from_global(packed, nbytes, p + (uint64_t)m);
+                  }
+                }
+                have = true;
+              }
+              vis.vertex(valid, key, edge, label, lane, sub, ctx);
+            }
+            if (Visitor::kUniformRounds) vis.round_end();
+          }
+          __syncthreads();
+          ra = rb;
+        }
+      } else if (tid == 0) {
+        set_sticky(ctx.status, DBG_ERR_BAD_OFFSETS);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace dbg

@@ -27,6 +27,7 @@ NOALLOC_EXPORT_MAX_VERTICES = 1 << 19
 
 EXPORTED = [
     "dbg_create", "dbg_create_ex", "dbg_destroy", "dbg_reset", "dbg_set_tuning", "dbg_get_info",
+    "dbg_reserve_events", "dbg_enable_kernel_timing", "dbg_kernel_times",
     "dbg_insert_reads", "dbg_insert_reads_host", "dbg_insert_batch", "dbg_get_status", "dbg_stats",
     "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
     "dbg_probe_random_sectors",
@@ -44,12 +45,15 @@ class DbgError(RuntimeError):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("tile_reads", ctypes.c_int),
-                ("grid_ctas", ctypes.c_int), ("warp_aggregate", ctypes.c_int)]
+                ("grid_ctas", ctypes.c_int), ("warp_aggregate", ctypes.c_int),
+                ("insert_path", ctypes.c_int), ("apply_unroll", ctypes.c_int),
+                ("apply_counters", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("n_slots", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
-                ("max_probes", ctypes.c_uint32), ("device", ctypes.c_int)]
+                ("max_probes", ctypes.c_uint32), ("device", ctypes.c_int),
+                ("event_capacity", ctypes.c_uint64)]
 
 
 class BatchItem(ctypes.Structure):
@@ -77,6 +81,9 @@ def load() -> ctypes.CDLL:
         "dbg_reset": (I, [P, P]),
         "dbg_set_tuning": (I, [P, ctypes.POINTER(Tuning)]),
         "dbg_get_info": (I, [P, ctypes.POINTER(Info)]),
+        "dbg_reserve_events": (I, [P, U64]),
+        "dbg_enable_kernel_timing": (I, [P, I]),
+        "dbg_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(I)]),
         "dbg_insert_reads": (I, [P, P, P, U64, P]),
         "dbg_insert_reads_host": (I, [P, P, P, U64, P]),
         "dbg_insert_batch": (I, [ctypes.POINTER(BatchItem), I, P]),
@@ -185,12 +192,37 @@ class Graph:
         inf = Info()
         _check(load().dbg_get_info(self.handle, ctypes.byref(inf)), "dbg_get_info")
         return {"k": inf.k, "n_slots": inf.n_slots, "table_bytes": inf.table_bytes,
-                "max_probes": inf.max_probes, "device": inf.device}
+                "max_probes": inf.max_probes, "device": inf.device,
+                "event_capacity": inf.event_capacity}
 
     def set_tuning(self, block_threads: int = 0, tile_reads: int = 0, grid_ctas: int = 0,
-                   warp_aggregate: int = -1) -> None:
-        t = Tuning(block_threads, tile_reads, grid_ctas, warp_aggregate)
+                   warp_aggregate: int = -1, insert_path: int = 0, apply_unroll: int = 0,
+                   apply_counters: int = 0) -> None:
+        """Launch shape and path of the insert (``insert_path``: 0 auto, 1 direct,
+        2 binned; ``apply_unroll``: binned apply events per thread, 4/8/16;
+        ``apply_counters``: binned apply work counters, 1..64); the built graph
+        does not depend on any of these."""
+        t = Tuning(block_threads, tile_reads, grid_ctas, warp_aggregate, insert_path, apply_unroll,
+                   apply_counters)
         _check(load().dbg_set_tuning(self.handle, ctypes.byref(t)), "dbg_set_tuning")
+
+    KERNELS = ("direct", "bin_count", "bin_scan", "bin_scatter", "bin_apply", "direct_fallback")
+
+    def enable_kernel_timing(self, calls: int) -> None:
+        """Record CUDA events around each kernel of the next insert calls (keep ``calls``)."""
+        _check(load().dbg_enable_kernel_timing(self.handle, int(calls)), "dbg_enable_kernel_timing")
+
+    def kernel_times(self, max_calls: int = 1024) -> np.ndarray:
+        """[calls, 6] kernel durations in ms (-1: not launched), oldest call first."""
+        buf = (ctypes.c_float * (6 * max_calls))()
+        n = ctypes.c_int()
+        _check(load().dbg_kernel_times(self.handle, buf, max_calls, ctypes.byref(n)),
+               "dbg_kernel_times")
+        return np.frombuffer(buf, dtype=np.float32)[: 6 * n.value].reshape(n.value, 6).copy()
+
+    def reserve_events(self, events: int = 0) -> None:
+        """Size the binned insert's event buffer (0 = default, 4 per slot)."""
+        _check(load().dbg_reserve_events(self.handle, int(events)), "dbg_reserve_events")
 
     # -- build --------------------------------------------------------------
     def reset(self, stream=None) -> None:

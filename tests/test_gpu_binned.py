@@ -1,0 +1,138 @@
+"""The binned insert (events grouped by table region, applied region by
+region) against the oracle, bit for bit, including its fall-back to the
+direct kernel and its interplay with streams, resets and errors."""
+
+import numpy as np
+import pytest
+
+from gpu_util import assert_same_graph, capacity_for, oracle_export, to_device
+from paper_2401_02756_gb300 import build, dbg, synth
+
+pytestmark = pytest.mark.gpu
+
+MULTI_REGION = 5_000_000  # slots: five regions of 2^20 slots
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+    dbg.load()
+
+
+def binned_graph(rs, capacity=MULTI_REGION, **tuning):
+    g = dbg.Graph(rs.k, capacity)
+    g.set_tuning(insert_path=2, **tuning)
+    return g
+
+
+@pytest.mark.parametrize("k", [2, 5, 21, 31, 32])
+def test_binned_matches_oracle(k):
+    rs = synth.ragged_reads(3000, 300, k, 2000 + k, lead=k % 5)
+    g = binned_graph(rs)
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert g.status() == dbg.OK
+    if k <= 31:
+        assert g.info()["event_capacity"] > 0
+    assert_same_graph(g.export(), oracle_export(rs))
+    g.close()
+
+
+def test_binned_single_region_table():
+    rs = synth.ragged_reads(2000, 200, 21, 33)
+    g = binned_graph(rs, capacity=capacity_for(rs))
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert_same_graph(g.export(), oracle_export(rs))
+    g.close()
+
+
+def test_binned_falls_back_when_events_do_not_fit():
+    rs = synth.ragged_reads(2000, 200, 21, 34)
+    g = binned_graph(rs)
+    g.reserve_events(1000)  # far fewer than the vertex positions
+    assert g.info()["event_capacity"] == 1000
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert g.status() == dbg.OK
+    assert_same_graph(g.export(), oracle_export(rs))
+    g.close()
+
+
+def test_binned_calls_on_two_streams_and_repeated():
+    import torch
+    rs = synth.ragged_reads(2500, 220, 25, 35, lead=2)
+    g = binned_graph(rs, capacity=MULTI_REGION)
+    packed, offsets = to_device(rs)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    cuts = [0, 600, 1700, rs.n_reads]
+    for i in range(3):
+        g.insert(packed, offsets[cuts[i]:cuts[i + 1] + 1], stream=s1 if i % 2 else s2)
+    torch.cuda.synchronize()
+    assert_same_graph(g.export(), oracle_export(rs))
+    # a second pass doubles every counter and adds no vertex
+    g.insert(packed, offsets)
+    keys, counts = g.export()
+    ek, ec = oracle_export(rs)
+    assert np.array_equal(keys, ek) and np.array_equal(counts, 2 * ec)
+    g.reset()
+    g.insert(packed, offsets)
+    assert_same_graph(g.export(), oracle_export(rs))
+    g.close()
+
+
+def test_binned_with_host_buffers_and_low_complexity():
+    reads = ["A" * 150] * 200 + ["AC" * 75] * 100
+    rs0 = synth.ragged_reads(1500, 200, 31, 36)
+    rs = synth.from_strings(reads + [rs0.read_ascii(i) for i in range(rs0.n_reads)], 31)
+    g = binned_graph(rs)
+    g.insert_host(rs.packed, rs.offsets)
+    assert g.status() == dbg.OK
+    assert_same_graph(g.export(), oracle_export(rs))
+    g.close()
+
+
+def test_binned_capacity_overflow_is_reported():
+    rs = synth.ragged_reads(800, 150, 21, 37)
+    g = binned_graph(rs, capacity=300)
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert g.status() == dbg.ERR_CAPACITY
+    g.close()
+
+
+def test_auto_path_picks_binned_for_large_tables():
+    rs = synth.ragged_reads(1000, 150, 21, 38)
+    g = dbg.Graph(rs.k, (256 << 20) // 32)  # exactly the automatic threshold
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert g.info()["event_capacity"] > 0
+    assert_same_graph(g.export(), oracle_export(rs))
+    g.close()
+    small = dbg.Graph(rs.k, capacity_for(rs))
+    small.insert(packed, offsets)
+    assert small.info()["event_capacity"] == 0
+    small.close()
+
+
+def test_kernel_timer_records_the_kernels_each_path_launches():
+    rs = synth.ragged_reads(1500, 200, 21, 39)
+    packed, offsets = to_device(rs)
+    for path, launched in ((1, [0]), (2, [1, 2, 3, 4, 5])):
+        g = dbg.Graph(rs.k, MULTI_REGION)
+        g.set_tuning(insert_path=path)
+        g.enable_kernel_timing(4)
+        for _ in range(6):  # more calls than kept: the oldest are dropped
+            g.insert(packed, offsets)
+        t = g.kernel_times()
+        assert t.shape == (4, 6)
+        for j in range(6):
+            if j in launched:
+                assert (t[:, j] >= 0).all(), (path, j, t)
+            else:
+                assert (t[:, j] == -1).all(), (path, j, t)
+        g.close()
