@@ -66,6 +66,7 @@ typedef struct dbg_tuning {
   int insert_path;    /* 0: automatic; 1: direct; 2: binned (k <= 31; see dbg_insert_reads) */
   int apply_unroll;   /* binned apply: events in flight per thread, 4, 8 or 16 (0: default 4) */
   int apply_counters; /* binned apply: work counters the warps draw chunks from, 1..64 (0: 16) */
+  int region_log2;    /* binned: table region of 2^region_log2 slots, 16..26 (0: automatic) */
 } dbg_tuning;
 
 typedef struct dbg_info {

@@ -147,10 +147,14 @@ __global__ void __launch_bounds__(1024)
 
 // --- K1d --------------------------------------------------------------------
 
+// Events are staged in shared memory (kRoundEvents at a time), sorted there
+// by region (counting sort), and written out as runs: position = the slice's
+// run start in the region (reserved at the start of the slice, as long as the
+// count pass measured) + the events of the region already placed.
 template <int BLOCK>
 struct ScatterVisitor {
-  static_assert(BLOCK * kRun <= kRoundEvents, "a round must fit the flush buffer");
   static constexpr bool kUniformRounds = true;
+  static_assert(BLOCK * kRun <= kRoundEvents, "a round must fit the flush buffer");
   uint64_t *ev;        // kRoundEvents, in vertex order
   uint64_t *sorted;    // kRoundEvents, in region order
   uint16_t *pid;       // region of ev[i] (kNoPart: no event)
@@ -188,7 +192,7 @@ struct ScatterVisitor {
     __shared__ uint32_t s_total;
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // exclusive prefix over the regions; each region's slot in the output
+    // exclusive prefix over the regions; each region's place in the output
     const int per = (parts + BLOCK - 1) / BLOCK;
     const int p0 = min(parts, tid * per), p1 = min(parts, p0 + per);
     uint32_t local = 0;
@@ -296,30 +300,32 @@ __global__ void __launch_bounds__(BLOCK)
 
 // --- K1e --------------------------------------------------------------------
 
-// Each warp takes chunks of 32*U consecutive events (no block barriers).
-// Chunk j is handed out by counter j % n_ctr: the counters advance side by
-// side, so the chunks in flight stay close together in the event order (the
-// table window they touch stays in L2) while no single counter is hammered
-// by every warp.  A warp asks for its next chunk before working on the
-// current one.  A lane advances the probes of its U events in lock step:
-// every round first looks at the key words that arrived (a match counts the
-// label; an empty slot gets an atomicCAS; another key moves the probe on),
-// then has all the new loads and CASes of the round in flight together.
-template <int BLOCK, int U>
+// Each warp takes chunks of 32*M consecutive events (no block barriers),
+// staged in shared memory with one coalesced load.  Chunk j is handed out by
+// counter j % n_ctr: the counters advance side by side, so the chunks in
+// flight stay close together in the event order (the table window they touch
+// stays in L2) while no single counter is hammered by every warp.  A lane
+// then works through its column of the chunk with U probe slots: every round
+// it first looks at the key words that arrived (a match counts the label; an
+// empty slot gets an atomicCAS; another key moves the probe on) and then
+// refills every finished slot with its next event and that event's first key
+// load.  A long probe chain so holds up one slot, not the lane or the warp.
+template <int BLOCK, int U, int M>
 __global__ void __launch_bounds__(BLOCK)
     k_bin_apply(const uint64_t *__restrict__ ev, const unsigned long long *total_ptr,
                 const uint32_t *use_binned, Slot *table, uint64_t n_slots, uint32_t max_probes,
                 uint32_t *status, unsigned long long *ctrs, int n_ctr) {
   if (ld_volatile_u32(use_binned) == 0u) return;
-  const int lane = threadIdx.x & 31;
+  __shared__ uint64_t s_ev[BLOCK / 32][32 * M];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint64_t *my = s_ev[wib];
   const uint64_t total = *total_ptr;
-  constexpr uint64_t kChunk = 32 * U;
+  constexpr uint64_t kChunk = 32 * M;
   const uint64_t n_chunks = (total + kChunk - 1) / kChunk;
   const int gwarp = (int)((blockIdx.x * (uint64_t)BLOCK + threadIdx.x) >> 5);
   int k = gwarp % n_ctr;  // the counter this warp draws from
   int tried = 0;          // counters found exhausted
-  // next chunk index (or n_chunks when every counter is exhausted); lane 0 only
-  auto draw = [&]() -> uint64_t {
+  auto draw = [&]() -> uint64_t {  // lane 0 only
     while (tried < n_ctr) {
       if (ld_volatile_u32(status) != 0u) return n_chunks;
       const uint64_t j = atomicAdd(&ctrs[k], 1ull) * (uint64_t)n_ctr + (uint64_t)k;
@@ -336,40 +342,34 @@ __global__ void __launch_bounds__(BLOCK)
     unsigned long long next = 0;
     if (lane == 0) next = draw();
     const uint64_t c0 = c * kChunk;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const uint64_t i = c0 + (uint64_t)j * 32 + lane;
+      my[j * 32 + lane] = i < total ? __ldcs(ev + i) : kEmpty;
+    }
+    __syncwarp();
     uint64_t e[U], s[U];
     unsigned long long cur[U];
-    uint32_t pend = 0, cas_done = 0, probes[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = c0 + (uint64_t)u * 32 + lane;
-      e[u] = i < total ? __ldcs(ev + i) : kEmpty;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      probes[u] = 0;
-      if (e[u] != kEmpty) {
-        s[u] = home_slot(e[u] >> 3, n_slots);
-        cur[u] = ld_relaxed_u64(&table[s[u]].key);
-        pend |= 1u << u;
-      }
-    }
-    while (pend) {
+    uint32_t probes[U];
+    uint32_t active = 0, cas_done = 0;
+    int nj = 0;  // next event of this lane's column
+    do {
+      // 1. look at what arrived; issue each slot's next operation
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (!(pend & (1u << u))) continue;
+        if (!(active & (1u << u))) continue;
         const unsigned long long key = e[u] >> 3;
         if (cur[u] == key) {
           if (e[u] & 4ull) atomicAdd(&table[s[u]].cnt[e[u] & 3ull], 1u);
-          pend &= ~(1u << u);
+          active &= ~(1u << u);
         } else if (cur[u] == kEmpty && !(cas_done & (1u << u))) {
-          // claim it; the returned word decides next round (ours, or taken)
           const unsigned long long prev = atomicCAS(&table[s[u]].key, kEmpty, key);
           cur[u] = prev == kEmpty ? key : prev;
           cas_done |= 1u << u;
         } else {
           if (++probes[u] >= max_probes) {
             set_sticky(status, DBG_ERR_CAPACITY);
-            pend &= ~(1u << u);
+            active &= ~(1u << u);
             continue;
           }
           if (++s[u] == n_slots) s[u] = 0;
@@ -377,7 +377,21 @@ __global__ void __launch_bounds__(BLOCK)
           cas_done &= ~(1u << u);
         }
       }
-    }
+      // 2. refill finished slots with the column's next events
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if ((active & (1u << u)) || nj >= M) continue;
+        e[u] = my[nj * 32 + lane];
+        ++nj;
+        if (e[u] == kEmpty) continue;
+        s[u] = home_slot(e[u] >> 3, n_slots);
+        cur[u] = ld_relaxed_u64(&table[s[u]].key);
+        probes[u] = 0;
+        cas_done &= ~(1u << u);
+        active |= 1u << u;
+      }
+    } while (active != 0u || nj < M);
+    __syncwarp();
     c = __shfl_sync(kFull, next, 0);
   }
 }
@@ -390,9 +404,10 @@ int ceil_log2(uint64_t x) {
 
 }  // namespace
 
-BinGeometry bin_geometry(uint64_t n_slots) {
+BinGeometry bin_geometry(uint64_t n_slots, int region_log2) {
   BinGeometry g;
-  g.shift = std::max(kBinMinShift, ceil_log2((n_slots + kMaxParts - 1) / kMaxParts));
+  g.shift = std::max(region_log2 > 0 ? region_log2 : kBinMinShift,
+                     ceil_log2((n_slots + kMaxParts - 1) / kMaxParts));
   g.parts = (int)((n_slots + (1ull << g.shift) - 1) >> g.shift);
   return g;
 }
@@ -455,10 +470,11 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events) {
 template <int B, int U>
 int launch_apply(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int sms, int n_ctr,
                  cudaStream_t s) {
+  constexpr int M = 16;  // events per lane per chunk
   int per_sm = 0;
-  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_apply<B, U>, B, 0));
+  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_apply<B, U, M>, B, 0));
   const int grid = std::max(1, per_sm) * sms;
-  k_bin_apply<B, U><<<grid, B, 0, s>>>(h->bin_ev, mv.begin + geo.parts, mv.flag, h->table,
+  k_bin_apply<B, U, M><<<grid, B, 0, s>>>(h->bin_ev, mv.begin + geo.parts, mv.flag, h->table,
                                        h->n_slots, h->max_probes, h->d_status, mv.apply_ctr,
                                        n_ctr);
   DBG_CK(cudaGetLastError());
@@ -470,7 +486,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   constexpr int B = 256;
   const dbg_tuning t = resolve_tuning(tuning);
   const int tile_reads = std::min(t.tile_reads, B);
-  const BinGeometry geo = bin_geometry(h->n_slots);
+  const BinGeometry geo = bin_geometry(h->n_slots, t.region_log2);
   const uint64_t slices = std::min<uint64_t>(tiles, kBinSlices);
   const MetaView mv = meta_view(h);
 

@@ -11,7 +11,7 @@ constexpr uint64_t kBinMinEvents = 16ull << 20;       // smallest event buffer
 constexpr uint64_t kBinEventsPerSlot = 4;             // default event buffer: 4 events per slot
 
 constexpr uint64_t kBinSlices = 4096;                // count/scatter work units, at most
-constexpr int kBinMinShift = 20;                     // regions of at least 2^20 slots (32 MiB)
+constexpr int kBinMinShift = 18;                     // automatic: regions of at least 2^18 slots (8 MiB)
 
 constexpr int kBinApplyCounters = 64;                // apply: chunk counters, at most
 
@@ -27,7 +27,9 @@ struct BinGeometry {
   int parts;
 };
 
-BinGeometry bin_geometry(uint64_t n_slots);
+// Regions of 2^region_log2 slots (0: automatic), widened until there are at
+// most kBinMaxParts of them.
+BinGeometry bin_geometry(uint64_t n_slots, int region_log2);
 
 // Make sure the handle holds an event buffer of at least `events` events
 // (0: the default size) and the meta area.

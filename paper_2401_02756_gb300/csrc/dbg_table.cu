@@ -251,6 +251,7 @@ extern "C" int dbg_set_tuning(dbg_handle h, const dbg_tuning *t) {
   if (r.apply_unroll != 0 && r.apply_unroll != 4 && r.apply_unroll != 8 && r.apply_unroll != 16)
     return DBG_ERR_INVALID_ARG;
   if (r.apply_counters < 0 || r.apply_counters > 64) return DBG_ERR_INVALID_ARG;
+  if (r.region_log2 != 0 && (r.region_log2 < 16 || r.region_log2 > 26)) return DBG_ERR_INVALID_ARG;
   h->tuning = r;
   return DBG_OK;
 }

@@ -232,12 +232,15 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
           }
           const uint64_t v_lo = s_vpre[ra], v_hi = s_vpre[rb];
           const uint64_t mask = (1ull << (2 * m)) - 1ull;
+          const uint64_t wbase = wb0 << 2;  // base position of the window's first word
           int r = ra;
           for (uint64_t base = v_lo; base < v_hi; base += (uint64_t)BLOCK * R) {
             if (!Visitor::kUniformRounds && vis.stop(lane)) break;
             uint64_t v = base + (uint64_t)tid * R;
             uint64_t key = kEmpty;
             uint32_t label = 0;
+            // the read holding position v: vertex range [vr0, vr1), bases end at pend
+            uint64_t vr1 = 0, p = 0, pend = 0;
             bool have = false;
 #pragma unroll
             for (int sub = 0; sub < R; ++sub, ++v) {
@@ -245,24 +248,25 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
               bool edge = false;
               if (valid) {
                 bool fresh = !have;
-                while (s_vpre[r + 1] <= v) {
-                  ++r;
+                if (fresh || v >= vr1) {
+                  while (s_vpre[r + 1] <= v) ++r;
+                  vr1 = s_vpre[r + 1];
+                  p = s_off[r] - origin + (v - s_vpre[r]);
+                  pend = s_off[r + 1] - origin;
                   fresh = true;
+                } else {
+                  ++p;
                 }
-                const uint64_t j = v - s_vpre[r];
-                const uint64_t rs = s_off[r];
-                const uint64_t len = s_off[r + 1] - rs;
-                const uint64_t p = rs - origin + j;
-                edge = j + (uint64_t)k <= len;
+                edge = p + (uint64_t)k <= pend;
                 if (!gmode) {
-                  const uint64_t q = p - (wb0 << 2);
+                  const uint64_t q = p - wbase;
                   if (fresh) {
                     const uint32_t wi = (uint32_t)(q >> 5);
                     key = key_from_words(s_win[wi], s_win[wi + 1], (uint32_t)(q & 31) * 2, m);
                   } else {
                     key = ((key << 2) | label) & mask;
                   }
-                  const uint64_t qe = q + (uint64_t)m;
+                  const uint32_t qe = (uint32_t)q + (uint32_t)m;
                   label = (uint32_t)(s_win[qe >> 5] >> ((qe & 31) * 2)) & 3u;
                 } else {
                   if (fresh) {

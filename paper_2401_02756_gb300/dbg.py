@@ -47,7 +47,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("tile_reads", ctypes.c_int),
                 ("grid_ctas", ctypes.c_int), ("warp_aggregate", ctypes.c_int),
                 ("insert_path", ctypes.c_int), ("apply_unroll", ctypes.c_int),
-                ("apply_counters", ctypes.c_int)]
+                ("apply_counters", ctypes.c_int), ("region_log2", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -197,13 +197,14 @@ class Graph:
 
     def set_tuning(self, block_threads: int = 0, tile_reads: int = 0, grid_ctas: int = 0,
                    warp_aggregate: int = -1, insert_path: int = 0, apply_unroll: int = 0,
-                   apply_counters: int = 0) -> None:
+                   apply_counters: int = 0, region_log2: int = 0) -> None:
         """Launch shape and path of the insert (``insert_path``: 0 auto, 1 direct,
         2 binned; ``apply_unroll``: binned apply events per thread, 4/8/16;
-        ``apply_counters``: binned apply work counters, 1..64); the built graph
-        does not depend on any of these."""
+        ``apply_counters``: binned apply work counters, 1..64; ``region_log2``:
+        binned table region of 2^n slots); the built graph does not depend on
+        any of these."""
         t = Tuning(block_threads, tile_reads, grid_ctas, warp_aggregate, insert_path, apply_unroll,
-                   apply_counters)
+                   apply_counters, region_log2)
         _check(load().dbg_set_tuning(self.handle, ctypes.byref(t)), "dbg_set_tuning")
 
     KERNELS = ("direct", "bin_count", "bin_scan", "bin_scatter", "bin_apply", "direct_fallback")
