@@ -53,6 +53,8 @@ def parse_args():
                     help="insert launch shape, e.g. apply_unroll=4,insert_path=2 (graph unchanged)")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="print the random-sector probe rate over buffer sizes and exit")
+    ap.add_argument("--window-sweep", action="store_true",
+                    help="print only the sliding-window probe rates and exit")
     return ap.parse_args()
 
 
@@ -519,7 +521,7 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def run_probe_sweep():
+def run_probe_sweep(window_only=False):
     """Random 32-byte-sector probe (K5) rate over buffer sizes, one JSON line each."""
     import torch
 
@@ -528,7 +530,9 @@ def run_probe_sweep():
     _build.build()
     dbg.load()
     n_ops = 1 << 30
-    for n_slots in [1 << 18, 1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24, 1 << 26, 1 << 28, 633846003]:
+    sizes = [] if window_only else [1 << 18, 1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24, 1 << 26,
+                                    1 << 28, 633846003]
+    for n_slots in sizes:
         buf = torch.zeros(n_slots * 32, dtype=torch.uint8, device="cuda")
         for mode in (0, 1, 2):
             dbg.probe_random_sectors(buf, n_slots, 1 << 26, 3, mode, None)
@@ -543,12 +547,30 @@ def run_probe_sweep():
                               "ms": ms, "Gops": n_ops / ms / 1e6}), flush=True)
         del buf
         torch.cuda.empty_cache()
+    # a window sliding across a table-sized buffer (the binned apply's pattern)
+    n_slots = 633846003
+    buf = torch.zeros(n_slots * 32, dtype=torch.uint8, device="cuda")
+    n_ops = 2420000000
+    for flags in (0, 1):
+        for wlog in (15, 17, 19, 20, 21, 23):
+            dbg.probe_window(buf, n_slots, 1 << 26, 1 << wlog, 3, flags, None)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dbg.probe_window(buf, n_slots, n_ops, 1 << wlog, 9, flags, None)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            print(json.dumps({"n_slots": n_slots, "window_slots": 1 << wlog,
+                              "window_MB": (1 << wlog) * 32 / 2 ** 20,
+                              "mode": "window" + ("+evict_last" if flags else ""), "ms": ms,
+                              "Gops": n_ops / ms / 1e6}), flush=True)
 
 
 def main():
     args = parse_args()
-    if args.probe_sweep:
-        run_probe_sweep()
+    if args.probe_sweep or args.window_sweep:
+        run_probe_sweep(window_only=args.window_sweep)
     elif args.workload == "batch256" and args.impl == "ours":
         run_batch(args)
     elif args.impl == "reference":

@@ -51,7 +51,8 @@ typedef enum dbg_status {
   DBG_ERR_CUDA = 4,             /* a CUDA runtime call failed (see dbg_last_cuda_error) */
   DBG_ERR_BUFFER_TOO_SMALL = 5, /* export: max_n < number of vertices (n_out tells how many) */
   DBG_ERR_BAD_OFFSETS = 6,      /* sticky: the GPU saw offsets[r+1] < offsets[r] */
-  DBG_ERR_NOALLOC_LIMIT = 7     /* dbg_export_sorted_noalloc: graph larger than its fixed scratch */
+  DBG_ERR_NOALLOC_LIMIT = 7,    /* dbg_export_sorted_noalloc: graph larger than its fixed scratch */
+  DBG_ERR_NEEDS_GROW = 8        /* vertices were spilled (see dbg_set_spill): call dbg_grow */
 } dbg_status;
 
 typedef struct dbg_graph *dbg_handle;
@@ -64,9 +65,12 @@ typedef struct dbg_tuning {
   int grid_ctas;      /* CTAs in the persistent grid (default: SMs x resident CTAs per SM) */
   int warp_aggregate; /* 1: merge equal keys of a warp with __match_any_sync; 0: off; -1: default */
   int insert_path;    /* 0: automatic; 1: direct; 2: binned (k <= 31; see dbg_insert_reads) */
-  int apply_unroll;   /* binned apply: events in flight per thread, 4, 8 or 16 (0: default 4) */
+  int apply_unroll;   /* binned apply: probe slots per thread, 2, 4 or 8 (0: default 4) */
+  int apply_chunk;    /* binned apply: events per thread per work chunk, 4, 8 or 16 (0: 8) */
+  int apply_ctas;     /* binned apply: CTAs per SM (0: as many as fit) */
   int apply_counters; /* binned apply: work counters the warps draw chunks from, 1..64 (0: 16) */
   int region_log2;    /* binned: table region of 2^region_log2 slots, 16..26 (0: automatic) */
+  int apply_group;    /* binned apply: regions per launch (0: all regions in one launch) */
 } dbg_tuning;
 
 typedef struct dbg_info {
@@ -76,6 +80,7 @@ typedef struct dbg_info {
   uint32_t max_probes;  /* slots probed per vertex before DBG_ERR_CAPACITY */
   int device;           /* CUDA device the table lives on */
   uint64_t event_capacity; /* binned-insert event buffer, in events (0: not allocated) */
+  uint64_t spill_capacity; /* spill records (0: no spill buffer) */
 } dbg_info;
 
 /* Create an empty graph for k-mers of length k (2..32) with room for
@@ -171,15 +176,37 @@ typedef struct dbg_batch_item {
 } dbg_batch_item;
 
 /* Insert many independent read sets, each into its own graph (graphs may
- * differ in k and size), with ONE kernel launch on `stream` whose CTAs take
- * (item, read tile) work units from a shared queue.  Every graph must live
- * on the current device.  The result equals one dbg_insert_reads per item.
- * Errors: INVALID_ARG, OOM (descriptor upload), CUDA; sticky errors are
- * recorded in each item's own graph. */
+ * differ in k and size).  Graphs small enough for the direct path share
+ * launches: one kernel for up to 128 of them, its CTAs taking (item, read
+ * tile) work units from one index space.  Graphs that take the binned path
+ * (see dbg_insert_reads) are inserted with it, one after another.  Every graph
+ * must live on the current device; all work is on `stream`.  The result equals
+ * one dbg_insert_reads per item.  Errors: INVALID_ARG, OOM, CUDA; sticky
+ * errors are recorded in each item's own graph. */
 int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *stream);
 
+/* Grow-and-rebuild.  dbg_set_spill gives the graph a buffer of `records`
+ * 16-byte spill records (0 removes it): a vertex position that finds no
+ * matching or empty slot within max_probes is then kept there, with its
+ * label, instead of failing with DBG_ERR_CAPACITY (which remains the outcome
+ * when the buffer is full).  While records are pending the graph is
+ * incomplete: dbg_get_status, dbg_stats and dbg_export_sorted return
+ * DBG_ERR_NEEDS_GROW.  Synchronizes the device.  Errors: INVALID_ARG, OOM. */
+int dbg_set_spill(dbg_handle h, uint64_t records);
+
+/* Rebuild the graph in a new table of `new_capacity` slots (0: twice the
+ * current size): every vertex and its counters is re-inserted, then every
+ * pending spill record is replayed, so the graph is exactly the one a large
+ * enough table would have built.  Waits for `stream` and runs on it; the old
+ * table is released on success.  If the new table is itself too small,
+ * DBG_ERR_CAPACITY is returned and the graph is left as it was (old table and
+ * spill intact).  Errors: INVALID_ARG, OOM, CUDA, CAPACITY, and a sticky
+ * status other than DBG_OK (a graph that already lost events is not grown). */
+int dbg_grow(dbg_handle h, uint64_t new_capacity, void *stream);
+
 /* Wait for `stream`, then return the sticky status (DBG_OK, CAPACITY or
- * BAD_OFFSETS), or CUDA if a launch failed. */
+ * BAD_OFFSETS), DBG_ERR_NEEDS_GROW when spilled vertices are pending, or CUDA
+ * if a launch failed. */
 int dbg_get_status(dbg_handle h, void *stream);
 
 /* Wait for `stream`, then count the vertices and the edges (the sum of all
@@ -228,6 +255,62 @@ int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, ui
 int dbg_export_sorted_noalloc(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out,
                               uint64_t max_n, uint64_t *n_out, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Capacity prediction: a HyperLogLog sketch of the vertex keys.             */
+/* ------------------------------------------------------------------------ */
+
+#define DBG_SKETCH_REGISTERS 1024
+
+/* Sketch the distinct vertices of a read set (device buffers, conventions as
+ * dbg_insert_reads) so that a table can be sized before it is built (the
+ * paper sizes its table from the genome size, Section "Code organization").
+ * Every vertex position's key is hashed (MurmurHash3's finalizer after a fixed
+ * salt); the top 10 bits select one of DBG_SKETCH_REGISTERS registers, which
+ * keep the maximum of 1 + the leading zeros of the other 54 bits (HyperLogLog,
+ * Flajolet et al. 2007).  `registers` is a device array of
+ * DBG_SKETCH_REGISTERS + 1 uint32: it is zeroed, then filled; the last word
+ * receives DBG_ERR_BAD_OFFSETS if an offset decreases.  Asynchronous on
+ * `stream`.  The registers depend only on the set of distinct keys.
+ * Errors: INVALID_ARG, CUDA. */
+int dbg_sketch_reads(int k, const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads,
+                     uint32_t *registers, void *stream);
+
+/* Host helper: the HyperLogLog estimate of the number of distinct keys from
+ * DBG_SKETCH_REGISTERS registers in host memory (raw estimate with the
+ * small-range linear-counting correction); -1 for a NULL pointer. */
+double dbg_sketch_estimate(const uint32_t *registers);
+
+/* The capacity predictor's network: FP32, DBG_MLP_INPUTS -> DBG_MLP_HIDDEN ->
+ * DBG_MLP_HIDDEN -> 1 with ReLU, mapping a sketch's registers (divided by 64)
+ * to ln(distinct vertices).  All buffers are device memory owned by the
+ * caller; nothing is allocated.  Parameters (DBG_MLP_PARAMS floats):
+ * W1[64][1024] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3.  `work` holds
+ * dbg_mlp_work_floats(batch) floats.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+#define DBG_MLP_INPUTS 1024
+#define DBG_MLP_HIDDEN 64
+#define DBG_MLP_PARAMS 69825
+
+uint64_t dbg_mlp_work_floats(int batch);
+
+/* x[b][j] = registers[b * stride + j] / 64 for j < DBG_MLP_INPUTS. */
+int dbg_mlp_features(const uint32_t *registers, int64_t stride, int batch, float *x, void *stream);
+
+/* He-uniform weights from a counter-based hash of (seed, index); zero biases. */
+int dbg_mlp_init(float *params, uint64_t seed, void *stream);
+
+/* y[b] = network(x[b]) for b < batch (x: batch x DBG_MLP_INPUTS, row-major). */
+int dbg_mlp_forward(const float *params, const float *x, int batch, float *y, float *work,
+                    void *stream);
+
+/* One Adam step (step >= 1, learning rate lr, betas 0.9 / 0.999, eps 1e-8) on
+ * the mean of (y - target)^2 / 2 over the batch.  `grads`, `adam_m`, `adam_v`
+ * hold DBG_MLP_PARAMS floats each (the moments start at zero); *loss_out
+ * (device or host, may be NULL) receives the loss before the step. */
+int dbg_mlp_train_step(float *params, float *grads, float *adam_m, float *adam_v, int step,
+                       float lr, const float *x, const float *target, int batch, float *work,
+                       float *loss_out, void *stream);
+
 /* Host helper: pack n ASCII bases (A, C, G, T; upper case) into out, which
  * holds ceil(n/4) bytes, starting at base position `phase` (0..3) of out[0]
  * (bits of out[0] below the phase are preserved).  Any other symbol returns
@@ -254,6 +337,15 @@ const char *dbg_last_cuda_error(void);
  * The buffer's contents change.  Errors: INVALID_ARG, CUDA. */
 int dbg_probe_random_sectors(void *buf, uint64_t n_slots, uint64_t n_ops, uint64_t seed, int mode,
                              void *stream);
+
+/* As mode 1 above (load, then atomicAdd on the same slot), on a random slot
+ * of a window of `window_slots` slots that slides linearly from the start to
+ * the end of the buffer as the operation index grows -- the pattern of a
+ * region-ordered stream of table updates.  flags bit 0: give the accesses an
+ * L2 evict_last cache policy; bit 1: loads only; bit 2: atomicAdds only.
+ * Errors: INVALID_ARG, CUDA. */
+int dbg_probe_window(void *buf, uint64_t n_slots, uint64_t n_ops, uint64_t window_slots,
+                     uint64_t seed, int flags, void *stream);
 
 #ifdef __cplusplus
 }

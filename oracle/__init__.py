@@ -61,6 +61,8 @@ def _load():
     lib.oracle_free.restype = None
     lib.oracle_shard_of_keys.argtypes = [P, U64, I, U64, P]
     lib.oracle_shard_of_keys.restype = None
+    lib.oracle_sketch.argtypes = [P, P, U64, I, P]
+    lib.oracle_sketch.restype = I
     _lib = lib
     return lib
 
@@ -127,6 +129,32 @@ def shard_of_keys(keys: np.ndarray, k: int, shard_mod: int) -> np.ndarray:
     if keys.size:
         lib.oracle_shard_of_keys(keys.ctypes.data, keys.size, k, shard_mod, out.ctypes.data)
     return out
+
+
+def sketch(packed: np.ndarray, offsets: np.ndarray, k: int) -> np.ndarray:
+    """HyperLogLog registers (uint32[1024]) of the vertex keys of a read set."""
+    lib = _load()
+    packed = np.ascontiguousarray(packed, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    regs = np.zeros(1024, dtype=np.uint32)
+    st = lib.oracle_sketch(packed.ctypes.data if packed.size else None, offsets.ctypes.data,
+                           offsets.size - 1, k, regs.ctypes.data)
+    if st != 0:
+        raise RuntimeError(f"oracle_sketch failed with status {st}")
+    return regs
+
+
+def hll_estimate(regs: np.ndarray) -> float:
+    """HyperLogLog estimate (Flajolet et al. 2007): alpha_m m^2 / sum 2^-M_j,
+    with linear counting m ln(m/V) when the raw estimate is at most 2.5 m and
+    V registers are zero."""
+    m = float(regs.size)
+    alpha = 0.7213 / (1.0 + 1.079 / m)
+    raw = alpha * m * m / float(np.sum(np.ldexp(1.0, -regs.astype(np.int64))))
+    zeros = int(np.count_nonzero(regs == 0))
+    if raw <= 2.5 * m and zeros > 0:
+        return m * float(np.log(m / zeros))
+    return raw
 
 
 def decode_key(key: int, k: int) -> str:

@@ -370,3 +370,61 @@ void oracle_shard_of_keys(const uint64_t *keys, uint64_t n, int k, uint64_t shar
     out[i] = fnv1a(s, m) % shard_mod;
   }
 }
+
+/* ------------------------------------------------------------------------- */
+/* HyperLogLog registers of the vertex keys (for the sketch kernel's parity)  */
+/* ------------------------------------------------------------------------- */
+
+/* MurmurHash3's 64-bit finalizer, from its published definition. */
+static uint64_t murmur3_fmix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return x;
+}
+
+/* Registers (1024) of the HyperLogLog sketch (Flajolet et al. 2007) of the
+ * distinct (k-1)-mers that the build would make vertices: for each vertex
+ * position of each read of length >= k, hash = fmix64(key XOR salt), register
+ * = top 10 bits, value = max(value, 1 + leading zeros of the low 54 bits),
+ * 55 when those bits are all zero.  The salt is the 64-bit golden ratio
+ * constant. */
+int oracle_sketch(const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads, int k,
+                  uint32_t *regs) {
+  const uint64_t salt = 0x9E3779B97F4A7C15ULL;
+  if (!offsets || !regs || k < 2 || k > 32) return OR_ERR_ARG;
+  for (int j = 0; j < 1024; ++j) regs[j] = 0;
+  uint64_t maxlen = 0;
+  for (uint64_t r = 0; r < n_reads; ++r) {
+    if (offsets[r + 1] < offsets[r]) return OR_ERR_ARG;
+    uint64_t len = offsets[r + 1] - offsets[r];
+    if (len > maxlen) maxlen = len;
+  }
+  char *buf = (char *)malloc(maxlen + 1);
+  if (!buf) return OR_ERR_NOMEM;
+  const int m = k - 1;
+  for (uint64_t r = 0; r < n_reads; ++r) {
+    uint64_t len = offsets[r + 1] - offsets[r];
+    if (len < (uint64_t)k) continue;
+    unpack_range(packed, offsets[r], len, buf);
+    for (uint64_t j = 0; j + (uint64_t)m <= len; ++j) { /* vertex positions 0 .. len-k+1 */
+      uint64_t h = murmur3_fmix64(encode(buf + j, m) ^ salt);
+      uint32_t idx = (uint32_t)(h >> 54);
+      uint64_t rest = h << 10;
+      uint32_t rho = 1;
+      if (rest == 0) {
+        rho = 55;
+      } else {
+        while (!(rest & 0x8000000000000000ULL)) {
+          rest <<= 1;
+          ++rho;
+        }
+      }
+      if (rho > regs[idx]) regs[idx] = rho;
+    }
+  }
+  free(buf);
+  return OR_OK;
+}

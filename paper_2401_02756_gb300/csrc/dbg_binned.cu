@@ -37,7 +37,6 @@ namespace {
 constexpr int kMaxParts = kBinMaxParts;
 constexpr int kRun = 8;             // consecutive vertex positions per thread (rolled keys)
 constexpr int kRoundEvents = 2048;  // events buffered per scatter flush (256 threads x kRun)
-constexpr uint16_t kNoPart = 0xFFFFu;
 
 __device__ __forceinline__ uint64_t make_event(uint64_t key, bool edge, uint32_t label) {
   return (key << 3) | ((uint64_t)edge << 2) | (uint64_t)label;
@@ -147,47 +146,42 @@ __global__ void __launch_bounds__(1024)
 
 // --- K1d --------------------------------------------------------------------
 
-// Events are staged in shared memory (kRoundEvents at a time), sorted there
-// by region (counting sort), and written out as runs: position = the slice's
-// run start in the region (reserved at the start of the slice, as long as the
-// count pass measured) + the events of the region already placed.
+// A round of the tile walk gives every thread kRun events; each keeps them in
+// registers with its region and its rank in the region (a shared-memory
+// atomic), then the round is flushed: an exclusive prefix of the region
+// counts places the events in region order in shared memory (counting
+// sort), and they are written out as runs.  A run's position = the slice's
+// run start in the region (reserved at the start of the slice, as long as
+// the count pass measured) + the events of the region already placed.
 template <int BLOCK>
 struct ScatterVisitor {
   static constexpr bool kUniformRounds = true;
-  static_assert(BLOCK * kRun <= kRoundEvents, "a round must fit the flush buffer");
-  uint64_t *ev;        // kRoundEvents, in vertex order
+  static_assert(BLOCK * kRun == kRoundEvents, "one round is one flush");
   uint64_t *sorted;    // kRoundEvents, in region order
-  uint16_t *pid;       // region of ev[i] (kNoPart: no event)
-  uint16_t *rank;      // position of ev[i] within its region in this flush
   uint16_t *spid;      // region of sorted[j]
-  uint32_t *hist;      // parts: events per region in this flush
+  uint32_t *hist;      // parts: events per region in this round
   uint32_t *off;       // parts: exclusive prefix of hist
   unsigned long long *cur;    // parts: next global position of each region (this slice)
-  unsigned long long *gbase;  // parts: cur[p] - off[p] for this flush
+  unsigned long long *gbase;  // parts: cur[p] - off[p] for this round
   uint64_t *out;
   uint64_t cap;  // events the buffer holds: never store past it
   int shift, parts;
-  int n = 0;  // block-uniform: positions buffered
+  uint64_t ev[kRun];     // this thread's events of the round
+  uint32_t where[kRun];  // region << 16 | rank, or ~0 for no event
 
   __device__ void tile_begin() {}
   __device__ bool stop(int) { return false; }
   __device__ void vertex(bool valid, uint64_t key, bool edge, uint32_t label, int, int sub,
                          const VertexCtx &c) {
-    const int i = n + threadIdx.x * kRun + sub;
     if (valid) {
       const uint32_t p = (uint32_t)(home_slot(key, c.n_slots) >> shift);
-      ev[i] = make_event(key, edge, label);
-      pid[i] = (uint16_t)p;
-      rank[i] = (uint16_t)atomicAdd(&hist[p], 1u);
+      ev[sub] = make_event(key, edge, label);
+      where[sub] = (p << 16) | atomicAdd(&hist[p], 1u);
     } else {
-      pid[i] = kNoPart;
+      where[sub] = ~0u;
     }
   }
   __device__ void round_end() {
-    n += BLOCK * kRun;
-    if (n + BLOCK * kRun > kRoundEvents) flush();
-  }
-  __device__ void flush() {
     __shared__ unsigned long long s_w[BLOCK / 32];
     __shared__ uint32_t s_total;
     __syncthreads();
@@ -223,13 +217,15 @@ struct ScatterVisitor {
       run += h;
     }
     __syncthreads();
-    // counting sort into region order
-    for (int i = tid; i < n; i += BLOCK) {
-      const uint16_t p = pid[i];
-      if (p != kNoPart) {
-        const uint32_t j = off[p] + rank[i];
-        sorted[j] = ev[i];
-        spid[j] = p;
+    // counting sort of the registers into region order
+#pragma unroll
+    for (int sub = 0; sub < kRun; ++sub) {
+      const uint32_t w = where[sub];
+      if (w != ~0u) {
+        const uint32_t p = w >> 16;
+        const uint32_t j = off[p] + (w & 0xFFFFu);
+        sorted[j] = ev[sub];
+        spid[j] = (uint16_t)p;
       }
     }
     __syncthreads();
@@ -240,14 +236,13 @@ struct ScatterVisitor {
     }
     __syncthreads();
     for (int p = tid; p < parts; p += BLOCK) hist[p] = 0;
-    n = 0;
     __syncthreads();
   }
 };
 
 template <int BLOCK>
 constexpr size_t scatter_smem(int tile_reads, int parts) {
-  return tile_smem_bytes(tile_reads) + (size_t)kRoundEvents * (8 + 8 + 2 + 2 + 2) +
+  return tile_smem_bytes(tile_reads) + (size_t)kRoundEvents * (8 + 2) +
          (size_t)parts * (4 + 4 + 8 + 8) + 64;
 }
 
@@ -260,8 +255,6 @@ __global__ void __launch_bounds__(BLOCK)
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char *p = smem + tile_smem_bytes(tile_reads);
   ScatterVisitor<BLOCK> vis;
-  vis.ev = reinterpret_cast<uint64_t *>(p);
-  p += kRoundEvents * 8;
   vis.sorted = reinterpret_cast<uint64_t *>(p);
   p += kRoundEvents * 8;
   vis.gbase = reinterpret_cast<unsigned long long *>(p);
@@ -272,10 +265,6 @@ __global__ void __launch_bounds__(BLOCK)
   p += (size_t)parts * 4;
   vis.off = reinterpret_cast<uint32_t *>(p);
   p += (size_t)parts * 4;
-  vis.pid = reinterpret_cast<uint16_t *>(p);
-  p += kRoundEvents * 2;
-  vis.rank = reinterpret_cast<uint16_t *>(p);
-  p += kRoundEvents * 2;
   vis.spid = reinterpret_cast<uint16_t *>(p);
   vis.out = out;
   vis.cap = cap;
@@ -294,36 +283,44 @@ __global__ void __launch_bounds__(BLOCK)
     __syncthreads();
     for_each_vertex<BLOCK, 1, kRun>(pk, tile_reads, smem, vis, sl * T / slices,
                                     (sl + 1) * T / slices, 1);
-    if (vis.n > 0) vis.flush();
   }
 }
 
 // --- K1e --------------------------------------------------------------------
 
-// Each warp takes chunks of 32*M consecutive events (no block barriers),
-// staged in shared memory with one coalesced load.  Chunk j is handed out by
-// counter j % n_ctr: the counters advance side by side, so the chunks in
-// flight stay close together in the event order (the table window they touch
-// stays in L2) while no single counter is hammered by every warp.  A lane
-// then works through its column of the chunk with U probe slots: every round
-// it first looks at the key words that arrived (a match counts the label; an
-// empty slot gets an atomicCAS; another key moves the probe on) and then
-// refills every finished slot with its next event and that event's first key
-// load.  A long probe chain so holds up one slot, not the lane or the warp.
+// One launch applies the events of a group of consecutive regions (by
+// default all of them).  Each warp streams chunks of 32*M consecutive events
+// (no block barriers).
+// Chunk j is handed out by counter j % n_ctr: the counters advance side by
+// side, so the chunks in flight stay close together in the event order (the
+// table window they touch stays in L2) while no single counter is hammered
+// by every warp.  Every lane keeps U probe slots.  A round first looks, in
+// every slot, at the key word that arrived (a match counts the label; an
+// empty slot gets an atomicCAS; another key moves the probe on), then the
+// whole warp refills the free slots from the staged chunk -- lane by lane in
+// ballot order, so no lane idles while the chunk has events -- and, half way
+// through a chunk, loads the next chunk into registers so that it is ready
+// when the staged one runs out.
 template <int BLOCK, int U, int M>
 __global__ void __launch_bounds__(BLOCK)
-    k_bin_apply(const uint64_t *__restrict__ ev, const unsigned long long *total_ptr,
-                const uint32_t *use_binned, Slot *table, uint64_t n_slots, uint32_t max_probes,
-                uint32_t *status, unsigned long long *ctrs, int n_ctr) {
+    k_bin_apply(const uint64_t *__restrict__ ev_all, const unsigned long long *begin,
+                int part_first, int part_end, const uint32_t *use_binned, Slot *table,
+                uint64_t n_slots, uint32_t max_probes, uint32_t *status, unsigned long long *ctrs,
+                int n_ctr, SpillRecord *spill, uint64_t spill_cap,
+                unsigned long long *spill_count) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   __shared__ uint64_t s_ev[BLOCK / 32][32 * M];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint64_t *my = s_ev[wib];
-  const uint64_t total = *total_ptr;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint64_t *buf = s_ev[wib];
+  // this launch's events: those of regions [part_first, part_end)
+  const uint64_t e0 = begin[part_first];
+  const uint64_t total = begin[part_end] - e0;
+  const uint64_t *__restrict__ ev = ev_all + e0;
   constexpr uint64_t kChunk = 32 * M;
   const uint64_t n_chunks = (total + kChunk - 1) / kChunk;
   const int gwarp = (int)((blockIdx.x * (uint64_t)BLOCK + threadIdx.x) >> 5);
-  int k = gwarp % n_ctr;  // the counter this warp draws from
+  int k = gwarp % n_ctr;  // the counter this warp draws from (lane 0's copy counts)
   int tried = 0;          // counters found exhausted
   auto draw = [&]() -> uint64_t {  // lane 0 only
     while (tried < n_ctr) {
@@ -335,64 +332,99 @@ __global__ void __launch_bounds__(BLOCK)
     }
     return n_chunks;
   };
-  unsigned long long c = 0;
-  if (lane == 0) c = draw();
-  c = __shfl_sync(kFull, c, 0);
-  while (c < n_chunks) {
-    unsigned long long next = 0;
-    if (lane == 0) next = draw();
-    const uint64_t c0 = c * kChunk;
+  auto load_chunk = [&](uint64_t c, uint64_t (&dst)[M]) {
 #pragma unroll
     for (int j = 0; j < M; ++j) {
-      const uint64_t i = c0 + (uint64_t)j * 32 + lane;
-      my[j * 32 + lane] = i < total ? __ldcs(ev + i) : kEmpty;
+      const uint64_t i = c * kChunk + (uint64_t)j * 32 + lane;
+      dst[j] = (c < n_chunks && i < total) ? __ldcs(ev + i) : kEmpty;
     }
-    __syncwarp();
-    uint64_t e[U], s[U];
-    unsigned long long cur[U];
-    uint32_t probes[U];
-    uint32_t active = 0, cas_done = 0;
-    int nj = 0;  // next event of this lane's column
-    do {
-      // 1. look at what arrived; issue each slot's next operation
+  };
+
+  unsigned long long c = 0, nc = 0;
+  if (lane == 0) {
+    c = draw();
+    nc = draw();
+  }
+  c = __shfl_sync(kFull, c, 0);
+  nc = __shfl_sync(kFull, nc, 0);
+  uint64_t pre[M];
+  load_chunk(c, pre);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (!(active & (1u << u))) continue;
-        const unsigned long long key = e[u] >> 3;
-        if (cur[u] == key) {
-          if (e[u] & 4ull) atomicAdd(&table[s[u]].cnt[e[u] & 3ull], 1u);
+  for (int j = 0; j < M; ++j) buf[j * 32 + lane] = pre[j];
+  __syncwarp();
+  uint32_t head = 0;                                      // next staged event to hand out
+  uint32_t avail = c < n_chunks ? (uint32_t)kChunk : 0u;  // staged events
+  bool have_pre = false;
+
+  uint64_t e[U], s[U];
+  unsigned long long cur[U];
+  uint32_t probes[U];
+  uint32_t active = 0, cas_done = 0;
+  for (;;) {
+    // 1. look at what arrived; issue each slot's next operation
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!(active & (1u << u))) continue;
+      const unsigned long long key = e[u] >> 3;
+      if (cur[u] == key) {
+        if (e[u] & 4ull) atomicAdd(&table[s[u]].cnt[e[u] & 3ull], 1u);
+        active &= ~(1u << u);
+      } else if (cur[u] == kEmpty && !(cas_done & (1u << u))) {
+        const unsigned long long prev = atomicCAS(&table[s[u]].key, kEmpty, key);
+        cur[u] = prev == kEmpty ? key : prev;
+        cas_done |= 1u << u;
+      } else {
+        if (++probes[u] >= max_probes) {
+          spill_or_fail(spill, spill_cap, spill_count, status, key, (e[u] & 4ull) != 0,
+                        (uint32_t)(e[u] & 3ull));
           active &= ~(1u << u);
-        } else if (cur[u] == kEmpty && !(cas_done & (1u << u))) {
-          const unsigned long long prev = atomicCAS(&table[s[u]].key, kEmpty, key);
-          cur[u] = prev == kEmpty ? key : prev;
-          cas_done |= 1u << u;
-        } else {
-          if (++probes[u] >= max_probes) {
-            set_sticky(status, DBG_ERR_CAPACITY);
-            active &= ~(1u << u);
-            continue;
-          }
-          if (++s[u] == n_slots) s[u] = 0;
+          continue;
+        }
+        if (++s[u] == n_slots) s[u] = 0;
+        cur[u] = ld_relaxed_u64(&table[s[u]].key);
+        cas_done &= ~(1u << u);
+      }
+    }
+    // 2. half way through the staged chunk: fetch the next one into registers
+    if (!have_pre && nc < n_chunks && 2 * head >= avail) {
+      load_chunk(nc, pre);
+      have_pre = true;
+    }
+    // 3. the warp hands out staged events to free slots, in lane order
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool want = !(active & (1u << u));
+      const unsigned b = __ballot_sync(kFull, want);
+      const uint32_t pos = head + (uint32_t)__popc(b & lt_mask);
+      if (want && pos < avail) {
+        e[u] = buf[pos];
+        if (e[u] != kEmpty) {
+          s[u] = home_slot(e[u] >> 3, n_slots);
           cur[u] = ld_relaxed_u64(&table[s[u]].key);
+          probes[u] = 0;
           cas_done &= ~(1u << u);
+          active |= 1u << u;
         }
       }
-      // 2. refill finished slots with the column's next events
+      head = min(avail, head + (uint32_t)__popc(b));
+    }
+    // 4. staged chunk used up: stage the prefetched one, draw the one after
+    if (head >= avail) {
+      if (have_pre) {
+        __syncwarp();
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if ((active & (1u << u)) || nj >= M) continue;
-        e[u] = my[nj * 32 + lane];
-        ++nj;
-        if (e[u] == kEmpty) continue;
-        s[u] = home_slot(e[u] >> 3, n_slots);
-        cur[u] = ld_relaxed_u64(&table[s[u]].key);
-        probes[u] = 0;
-        cas_done &= ~(1u << u);
-        active |= 1u << u;
+        for (int j = 0; j < M; ++j) buf[j * 32 + lane] = pre[j];
+        __syncwarp();
+        head = 0;
+        avail = (uint32_t)kChunk;
+        have_pre = false;
+        unsigned long long nn = 0;
+        if (lane == 0) nn = draw();
+        nc = __shfl_sync(kFull, nn, 0);
+      } else if (!__any_sync(kFull, active != 0u)) {
+        break;  // nothing staged, nothing prefetched, nothing in flight
       }
-    } while (active != 0u || nj < M);
-    __syncwarp();
-    c = __shfl_sync(kFull, next, 0);
+    }
   }
 }
 
@@ -432,7 +464,7 @@ MetaView meta_view(dbg_handle h) {
   v.ctr = v.cursor + kBinMaxParts;
   v.flag = reinterpret_cast<uint32_t *>(v.ctr + 3);
   v.apply_ctr = v.ctr + 4;
-  v.hist = reinterpret_cast<uint32_t *>(v.apply_ctr + kBinApplyCounters);
+  v.hist = reinterpret_cast<uint32_t *>(v.apply_ctr + (size_t)kBinMaxParts * kBinApplyCounters);
   return v;
 }
 
@@ -467,18 +499,37 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events) {
     if (st_ != DBG_OK) return st_; \
   } while (0)
 
-template <int B, int U>
-int launch_apply(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int sms, int n_ctr,
-                 cudaStream_t s) {
-  constexpr int M = 16;  // events per lane per chunk
+template <int B, int U, int M>
+int launch_apply(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int sms,
+                 const dbg_tuning &t, cudaStream_t s) {
   int per_sm = 0;
   DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_apply<B, U, M>, B, 0));
+  if (t.apply_ctas > 0) per_sm = std::min(per_sm, t.apply_ctas);
   const int grid = std::max(1, per_sm) * sms;
-  k_bin_apply<B, U, M><<<grid, B, 0, s>>>(h->bin_ev, mv.begin + geo.parts, mv.flag, h->table,
-                                       h->n_slots, h->max_probes, h->d_status, mv.apply_ctr,
-                                       n_ctr);
+  // regions per launch (default: all of them in one launch)
+  const int group = t.apply_group > 0 ? std::min(t.apply_group, geo.parts) : geo.parts;
+  const int n_groups = (geo.parts + group - 1) / group;
+  DBG_CK(cudaMemsetAsync(mv.apply_ctr, 0,
+                         (size_t)n_groups * t.apply_counters * sizeof(unsigned long long), s));
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const int p0 = gi * group, p1 = std::min(geo.parts, p0 + group);
+    k_bin_apply<B, U, M><<<grid, B, 0, s>>>(
+        h->bin_ev, mv.begin, p0, p1, mv.flag, h->table, h->n_slots, h->max_probes, h->d_status,
+        mv.apply_ctr + (size_t)gi * t.apply_counters, t.apply_counters, h->d_spill, h->spill_cap,
+        h->d_spill_count);
+  }
   DBG_CK(cudaGetLastError());
   return DBG_OK;
+}
+
+template <int B, int U>
+int launch_apply_m(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int sms,
+                   const dbg_tuning &t, cudaStream_t s) {
+  switch (t.apply_chunk) {
+    case 4: return launch_apply<B, U, 4>(h, mv, geo, sms, t, s);
+    case 16: return launch_apply<B, U, 16>(h, mv, geo, sms, t, s);
+    default: return launch_apply<B, U, 8>(h, mv, geo, sms, t, s);
+  }
 }
 
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
@@ -498,7 +549,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
 
   // binned calls on one handle share its scratch: order them
   DBG_CK(cudaStreamWaitEvent(s, h->bin_done, 0));
-  DBG_CK(cudaMemsetAsync(mv.ctr, 0, (4 + kBinApplyCounters) * sizeof(unsigned long long), s));
+  DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, geo.parts * sizeof(unsigned long long), s));
   timer_mark(h, call, 1, s);
   {
@@ -529,9 +580,9 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   }
   timer_mark(h, call, 4, s);
   switch (t.apply_unroll) {
-    case 8: DBG_TRY(launch_apply<B, 8>(h, mv, geo, sms, t.apply_counters, s)); break;
-    case 16: DBG_TRY(launch_apply<B, 16>(h, mv, geo, sms, t.apply_counters, s)); break;
-    default: DBG_TRY(launch_apply<B, 4>(h, mv, geo, sms, t.apply_counters, s)); break;
+    case 2: DBG_TRY(launch_apply_m<B, 2>(h, mv, geo, sms, t, s)); break;
+    case 8: DBG_TRY(launch_apply_m<B, 8>(h, mv, geo, sms, t, s)); break;
+    default: DBG_TRY(launch_apply_m<B, 4>(h, mv, geo, sms, t, s)); break;
   }
   // the direct insert runs only if the events did not fit the buffer
   timer_mark(h, call, 5, s);

@@ -13,14 +13,14 @@ constexpr uint64_t kBinEventsPerSlot = 4;             // default event buffer: 4
 constexpr uint64_t kBinSlices = 4096;                // count/scatter work units, at most
 constexpr int kBinMinShift = 18;                     // automatic: regions of at least 2^18 slots (8 MiB)
 
-constexpr int kBinApplyCounters = 64;                // apply: chunk counters, at most
+constexpr int kBinApplyCounters = 64;                // apply: chunk counters per launch, at most
 
 // meta area: begin[kBinMaxParts + 1] | counts[kBinMaxParts] | cursor[kBinMaxParts] |
-// counters[4] (the last holds the flag) | apply counters[kBinApplyCounters] |
+// counters[4] (the last holds the flag) | apply counters[kBinMaxParts][kBinApplyCounters] |
 // slice histograms u32[kBinSlices][kBinMaxParts]
 constexpr size_t kBinMetaBytes =
     ((size_t)kBinMaxParts + 1) * 8 + 2 * (size_t)kBinMaxParts * 8 + 4 * 8 +
-    (size_t)kBinApplyCounters * 8 + (size_t)kBinSlices * kBinMaxParts * 4;
+    (size_t)kBinMaxParts * kBinApplyCounters * 8 + (size_t)kBinSlices * kBinMaxParts * 4;
 
 struct BinGeometry {
   int shift;  // region = slots [p << shift, (p + 1) << shift)

@@ -27,29 +27,6 @@
 namespace dbg {
 namespace {
 
-// Find the slot holding `key`, claiming an empty one if the key is absent.
-// Returns false after max_probes slots without success.
-__device__ __forceinline__ bool find_or_claim(Slot *table, uint64_t n_slots, uint32_t max_probes,
-                                              uint64_t key, uint64_t &slot_out) {
-  uint64_t s = home_slot(key, n_slots);
-  for (uint32_t i = 0; i < max_probes; ++i) {
-    unsigned long long cur = ld_relaxed_u64(&table[s].key);
-    if (cur == key) {
-      slot_out = s;
-      return true;
-    }
-    if (cur == kEmpty) {
-      unsigned long long prev = atomicCAS(&table[s].key, kEmpty, (unsigned long long)key);
-      if (prev == kEmpty || prev == key) {
-        slot_out = s;
-        return true;
-      }
-    }
-    if (++s == n_slots) s = 0;
-  }
-  return false;
-}
-
 template <bool AGG>
 struct InsertVisitor {
   static constexpr bool kUniformRounds = false;
@@ -71,8 +48,7 @@ struct InsertVisitor {
         uint64_t slot;
         if (find_or_claim(c.table, c.n_slots, c.max_probes, key, slot)) {
           if (edge) atomicAdd(&c.table[slot].cnt[label], 1u);
-        } else {
-          set_sticky(c.status, DBG_ERR_CAPACITY);
+        } else if (spill_or_fail(c.spill, c.spill_cap, c.spill_count, c.status, key, edge, label)) {
           *s_cap_hit = 1u;
         }
       }
@@ -85,13 +61,18 @@ struct InsertVisitor {
       if (valid && lane == leader) {
         ok = find_or_claim(c.table, c.n_slots, c.max_probes, key, slot) ? 1 : 0;
         if (!ok) {
-          set_sticky(c.status, DBG_ERR_CAPACITY);
-          *s_cap_hit = 1u;
+          // every lane of the group spills its own position below
+          ok = -1;
         }
       }
       slot = __shfl_sync(kFull, slot, leader);
       ok = __shfl_sync(kFull, ok, leader);
-      const bool add = valid && ok && edge;
+      if (valid && ok < 0) {
+        if (spill_or_fail(c.spill, c.spill_cap, c.spill_count, c.status, key, edge, label))
+          *s_cap_hit = 1u;
+        ok = 0;
+      }
+      const bool add = valid && ok > 0 && edge;
       const unsigned long long ek = add ? ((slot << 2) | label) : kEmpty;
       const unsigned grp = __match_any_sync(kFull, ek);
       if (add && lane == __ffs(grp) - 1)
@@ -155,6 +136,7 @@ dbg_tuning resolve_tuning(const dbg_tuning &t) {
   if (r.tile_reads <= 0 || r.tile_reads > r.block_threads) r.tile_reads = r.block_threads;
   if (r.warp_aggregate < 0) r.warp_aggregate = 0;
   if (r.apply_unroll <= 0) r.apply_unroll = 4;
+  if (r.apply_chunk <= 0) r.apply_chunk = 8;
   if (r.apply_counters <= 0) r.apply_counters = 16;
   return r;
 }

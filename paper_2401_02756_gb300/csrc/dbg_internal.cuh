@@ -27,6 +27,29 @@ struct __align__(32) Slot {
 };
 static_assert(sizeof(Slot) == 32, "slot must be one 32-byte sector");
 
+// A vertex position that found no slot within max_probes, kept for dbg_grow.
+struct SpillRecord {
+  unsigned long long key;
+  unsigned long long info;  // bit 2: the position starts a k-mer; bits 0-1: its label
+};
+
+// Keep a vertex that found no slot, or fail with DBG_ERR_CAPACITY when there
+// is no spill buffer or it is full.  Returns true when the insert must stop.
+__device__ __forceinline__ bool spill_or_fail(SpillRecord *spill, uint64_t spill_cap,
+                                              unsigned long long *spill_count, uint32_t *status,
+                                              uint64_t key, bool edge, uint32_t label) {
+  if (spill != nullptr) {
+    const unsigned long long at = atomicAdd(spill_count, 1ull);
+    if (at < spill_cap) {
+      spill[at].key = key;
+      spill[at].info = ((unsigned long long)edge << 2) | label;
+      return false;
+    }
+  }
+  atomicCAS(status, 0u, (uint32_t)DBG_ERR_CAPACITY);
+  return true;
+}
+
 // One read set to insert into one table (a batch is an array of these).
 struct ItemDesc {
   const uint8_t *packed;     // 2-bit stream, byte 0 holds base `origin`
@@ -41,6 +64,9 @@ struct ItemDesc {
   uint64_t tile_begin;       // first global tile index of this item
   int vec_ok;                // packed is 16-byte aligned: vector loads allowed
   int pad_;
+  SpillRecord *spill;        // vertices that found no slot go here (null: fail instead)
+  uint64_t spill_cap;
+  unsigned long long *spill_count;
 };
 
 // MurmurHash3's 64-bit finalizer (Appleby, public domain): a bijective mix
@@ -64,6 +90,41 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   return v;
 }
 
+// An L2 cache policy that keeps the lines it touches ahead of others
+// (evict_last) for the whole access.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64_hint(const unsigned long long *p,
+                                                                   uint64_t pol) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.L2::cache_hint.u64 %0, [%1], %2;"
+               : "=l"(v)
+               : "l"(p), "l"(pol)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_add_u32_hint(uint32_t *p, uint32_t v, uint64_t pol) {
+  asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v),
+               "l"(pol)
+               : "memory");
+}
+
+__device__ __forceinline__ unsigned long long cas_u64_hint(unsigned long long *p,
+                                                           unsigned long long cmp,
+                                                           unsigned long long val, uint64_t pol) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.cas.L2::cache_hint.b64 %0, [%1], %2, %3, %4;"
+               : "=l"(old)
+               : "l"(p), "l"(cmp), "l"(val), "l"(pol)
+               : "memory");
+  return old;
+}
+
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
   return *(const volatile uint32_t *)p;
 }
@@ -85,6 +146,32 @@ __device__ __forceinline__ uint64_t key_from_words(uint64_t lo, uint64_t hi, uin
   return reverse_pairs(x) >> (64 - 2 * m);
 }
 
+// Find the slot holding `key`, claiming an empty one if the key is absent
+// (Alg. 4's search and Alg. 3's insertion, as open addressing: linear
+// probing from the home slot, a relaxed load first, atomicCAS only on EMPTY).
+// Returns false after max_probes slots without success.
+__device__ __forceinline__ bool find_or_claim(Slot *table, uint64_t n_slots, uint32_t max_probes,
+                                              uint64_t key, uint64_t &slot_out) {
+  uint64_t s = home_slot(key, n_slots);
+  for (uint32_t i = 0; i < max_probes; ++i) {
+    unsigned long long cur = ld_relaxed_u64(&table[s].key);
+    if (cur == key) {
+      slot_out = s;
+      return true;
+    }
+    if (cur == kEmpty) {
+      unsigned long long prev = atomicCAS(&table[s].key, kEmpty, (unsigned long long)key);
+      if (prev == kEmpty || prev == key) {
+        slot_out = s;
+        return true;
+      }
+    }
+    if (++s == n_slots) s = 0;
+  }
+  return false;
+}
+
+
 }  // namespace dbg
 
 // The handle.
@@ -93,9 +180,13 @@ struct dbg_graph {
   int device = 0;
   uint64_t n_slots = 0;
   uint32_t max_probes = 0;
+  bool max_probes_auto = true;  // max_probes follows the table size
   dbg::Slot *table = nullptr;
   uint32_t *d_status = nullptr;
   unsigned long long *d_acc = nullptr;  // [2]: vertices, edges (stats)
+  unsigned long long *d_spill_count = nullptr;  // spilled vertex positions
+  dbg::SpillRecord *d_spill = nullptr;
+  uint64_t spill_cap = 0;
   dbg_tuning tuning{};                  // as set by the user (0 = auto)
   int sm_count = 0;
   // staging for dbg_insert_reads_host
@@ -134,6 +225,8 @@ void timer_mark(dbg_handle h, int call, int m, cudaStream_t s);
 
 // Error plumbing shared by the entry points (host side).
 int cuda_fail(cudaError_t e, const char *what);
+int launch_grow(dbg_handle h, uint64_t new_capacity, cudaStream_t s);
+
 #define DBG_CK(call)                                        \
   do {                                                      \
     cudaError_t e_ = (call);                                \

@@ -1,0 +1,106 @@
+// K7: HyperLogLog sketch of a read set's vertex keys, the input of the
+// capacity predictor (the table must be sized before the build; the number of
+// distinct vertices is what sizes it).
+//
+// For every vertex position (the same positions the insert visits) the key is
+// hashed with MurmurHash3's 64-bit finalizer after an XOR with a fixed salt
+// (so the sketch hash is unrelated to the table's slot hash); the top 10 bits
+// of the hash pick one of 1024 registers and the register keeps the maximum
+// of rho = 1 + the number of leading zeros of the remaining 54 bits
+// (Flajolet, Fusy, Gandouet, Meunier, "HyperLogLog", AofA 2007).  A maximum
+// does not depend on order or repetition, so the registers are a function of
+// the set of distinct keys only.
+#include <math.h>
+
+#include <algorithm>
+
+#include "dbg_tiles.cuh"
+
+namespace dbg {
+namespace {
+
+constexpr unsigned long long kSketchSalt = 0x9E3779B97F4A7C15ull;
+constexpr int kSketchRegs = DBG_SKETCH_REGISTERS;
+
+struct SketchVisitor {
+  static constexpr bool kUniformRounds = false;
+  uint32_t *s_reg;
+  __device__ void tile_begin() {}
+  __device__ bool stop(int) { return false; }
+  __device__ void round_end() {}
+  __device__ void vertex(bool valid, uint64_t key, bool, uint32_t, int, int, const VertexCtx &) {
+    if (!valid) return;
+    const uint64_t h = fmix64(key ^ kSketchSalt);
+    const uint32_t idx = (uint32_t)(h >> 54);
+    const uint64_t rest = h << 10;
+    const uint32_t rho = rest ? (uint32_t)__clzll(rest) + 1u : 55u;
+    atomicMax(&s_reg[idx], rho);
+  }
+};
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_sketch(const __grid_constant__ ItemPack<1> pk, int tile_reads, uint32_t *regs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *s_reg = reinterpret_cast<uint32_t *>(smem + tile_smem_bytes(tile_reads));
+  for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK) s_reg[j] = 0u;
+  __syncthreads();
+  SketchVisitor vis{s_reg};
+  for_each_vertex<BLOCK, 1, 8>(pk, tile_reads, smem, vis, blockIdx.x, pk.total_tiles, gridDim.x);
+  __syncthreads();
+  for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK)
+    if (s_reg[j]) atomicMax(&regs[j], s_reg[j]);
+}
+
+}  // namespace
+}  // namespace dbg
+
+extern "C" int dbg_sketch_reads(int k, const uint8_t *packed, const uint64_t *offsets,
+                                uint64_t n_reads, uint32_t *registers, void *stream) {
+  using namespace dbg;
+  if (k < 2 || k > 32 || !registers || (n_reads > 0 && (!packed || !offsets)))
+    return DBG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBG_CK(cudaMemsetAsync(registers, 0, (kSketchRegs + 1) * sizeof(uint32_t), s));
+  if (n_reads == 0) return DBG_OK;
+  constexpr int B = 256;
+  const int tile_reads = B;
+  ItemPack<1> pk{};
+  pk.n_items = 1;
+  pk.total_tiles = (n_reads + tile_reads - 1) / tile_reads;
+  ItemDesc &it = pk.d[0];
+  it.packed = packed;
+  it.offsets = offsets;
+  it.n_reads = n_reads;
+  it.origin = 0;
+  it.table = nullptr;
+  it.n_slots = 1;
+  it.status = registers + kSketchRegs;  // bad offsets are reported here
+  it.max_probes = 0;
+  it.k = k;
+  it.vec_ok = ((uintptr_t)packed & 15u) == 0 ? 1 : 0;
+  const size_t smem = tile_smem_bytes(tile_reads) + kSketchRegs * sizeof(uint32_t);
+  int dev = 0, sms = 0, per_sm = 0;
+  DBG_CK(cudaGetDevice(&dev));
+  DBG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sketch<B>, B, smem));
+  const int grid = (int)std::min<uint64_t>(pk.total_tiles, (uint64_t)std::max(1, per_sm) * sms);
+  k_sketch<B><<<grid, B, smem, s>>>(pk, tile_reads, registers);
+  DBG_CK(cudaGetLastError());
+  return DBG_OK;
+}
+
+extern "C" double dbg_sketch_estimate(const uint32_t *registers) {
+  if (!registers) return -1.0;
+  const double m = dbg::kSketchRegs;
+  const double alpha = 0.7213 / (1.0 + 1.079 / m);
+  double sum = 0.0;
+  int zeros = 0;
+  for (int j = 0; j < dbg::kSketchRegs; ++j) {
+    sum += ldexp(1.0, -(int)registers[j]);
+    zeros += registers[j] == 0u;
+  }
+  const double raw = alpha * m * m / sum;
+  if (raw <= 2.5 * m && zeros > 0) return m * log(m / zeros);  // small-range correction
+  return raw;
+}

@@ -141,6 +141,9 @@ ItemDesc make_item(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
   it.k = h->k;
   it.tile_begin = 0;
   it.vec_ok = ((uintptr_t)packed & 15u) == 0 ? 1 : 0;
+  it.spill = h->d_spill;
+  it.spill_cap = h->spill_cap;
+  it.spill_count = h->d_spill_count;
   return it;
 }
 
@@ -163,6 +166,7 @@ extern "C" int dbg_create_ex(int k, uint64_t capacity, uint32_t max_probes, dbg_
   h->n_slots = capacity;
   h->max_probes = max_probes ? max_probes
                              : (uint32_t)std::min<uint64_t>(capacity, dbg::kDefaultMaxProbes);
+  h->max_probes_auto = max_probes == 0;
   int st = DBG_OK;
   do {
     cudaError_t e = cudaGetDevice(&h->device);
@@ -176,6 +180,7 @@ extern "C" int dbg_create_ex(int k, uint64_t capacity, uint32_t max_probes, dbg_
     if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaMalloc(status)"); break; }
     h->d_status = static_cast<uint32_t *>(small);
     h->d_acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 16);
+    h->d_spill_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 32);
     e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaStreamCreate"); break; }
     for (int i = 0; i < 2 && st == DBG_OK; ++i) {
@@ -217,6 +222,7 @@ extern "C" void dbg_destroy(dbg_handle h) {
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   cudaFree(h->bin_ev);
   cudaFree(h->bin_meta);
+  cudaFree(h->d_spill);
   if (h->bin_done) cudaEventDestroy(h->bin_done);
   dbg::destroy_timer(h);
   delete h;
@@ -230,6 +236,7 @@ extern "C" int dbg_reset(dbg_handle h, void *stream) {
   int st = dbg::launch_table_init(h->table, h->n_slots, s);
   if (st != DBG_OK) return st;
   DBG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s));
+  DBG_CK(cudaMemsetAsync(h->d_spill_count, 0, sizeof(unsigned long long), s));
   return DBG_OK;
 }
 
@@ -248,10 +255,14 @@ extern "C" int dbg_set_tuning(dbg_handle h, const dbg_tuning *t) {
   if (r.grid_ctas < 0) return DBG_ERR_INVALID_ARG;
   if (r.warp_aggregate < -1 || r.warp_aggregate > 1) return DBG_ERR_INVALID_ARG;
   if (r.insert_path < 0 || r.insert_path > 2) return DBG_ERR_INVALID_ARG;
-  if (r.apply_unroll != 0 && r.apply_unroll != 4 && r.apply_unroll != 8 && r.apply_unroll != 16)
+  if (r.apply_unroll != 0 && r.apply_unroll != 2 && r.apply_unroll != 4 && r.apply_unroll != 8)
     return DBG_ERR_INVALID_ARG;
+  if (r.apply_chunk != 0 && r.apply_chunk != 4 && r.apply_chunk != 8 && r.apply_chunk != 16)
+    return DBG_ERR_INVALID_ARG;
+  if (r.apply_ctas < 0 || r.apply_ctas > 32) return DBG_ERR_INVALID_ARG;
   if (r.apply_counters < 0 || r.apply_counters > 64) return DBG_ERR_INVALID_ARG;
   if (r.region_log2 != 0 && (r.region_log2 < 16 || r.region_log2 > 26)) return DBG_ERR_INVALID_ARG;
+  if (r.apply_group < 0) return DBG_ERR_INVALID_ARG;
   h->tuning = r;
   return DBG_OK;
 }
@@ -264,7 +275,35 @@ extern "C" int dbg_get_info(dbg_handle h, dbg_info *out) {
   out->max_probes = h->max_probes;
   out->device = h->device;
   out->event_capacity = h->bin_cap;
+  out->spill_capacity = h->spill_cap;
   return DBG_OK;
+}
+
+extern "C" int dbg_set_spill(dbg_handle h, uint64_t records) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  DBG_CK(cudaDeviceSynchronize());
+  unsigned long long pending = 0;
+  DBG_CK(cudaMemcpy(&pending, h->d_spill_count, sizeof(pending), cudaMemcpyDeviceToHost));
+  if (pending > 0) return DBG_ERR_NEEDS_GROW;  // records would be lost
+  cudaFree(h->d_spill);
+  h->d_spill = nullptr;
+  h->spill_cap = 0;
+  if (records == 0) return DBG_OK;
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, records * sizeof(dbg::SpillRecord));
+  if (e != cudaSuccess) return dbg::cuda_fail(e, "cudaMalloc(spill)");
+  h->d_spill = static_cast<dbg::SpillRecord *>(p);
+  h->spill_cap = records;
+  return DBG_OK;
+}
+
+extern "C" int dbg_grow(dbg_handle h, uint64_t new_capacity, void *stream) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  return dbg::launch_grow(h, new_capacity, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int dbg_enable_kernel_timing(dbg_handle h, int calls) {
@@ -486,7 +525,8 @@ extern "C" int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const dbg_tuning t = dbg::resolve_tuning(items[0].graph->tuning);
-  // one launch per group of up to kBatchItems non-empty items
+  // graphs whose tables take the binned path get it, one after another;
+  // the others share launches of up to kBatchItems items
   std::vector<dbg::ItemDesc> group;
   group.reserve(dbg::kBatchItems);
   uint64_t tiles = 0;
@@ -501,8 +541,14 @@ extern "C" int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *
     }
     if (i == n_items) break;
     if (items[i].n_reads == 0) continue;
-    dbg::ItemDesc it = dbg::make_item(items[i].graph, items[i].packed, items[i].offsets,
-                                      items[i].n_reads, 0);
+    dbg_handle h = items[i].graph;
+    dbg::ItemDesc it = dbg::make_item(h, items[i].packed, items[i].offsets, items[i].n_reads, 0);
+    if (want_binned(h)) {
+      const dbg_tuning th = dbg::resolve_tuning(h->tuning);
+      const int st = insert_one(h, it, (items[i].n_reads + th.tile_reads - 1) / th.tile_reads, s);
+      if (st != DBG_OK) return st;
+      continue;
+    }
     it.tile_begin = tiles;
     tiles += (items[i].n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
     group.push_back(it);
@@ -520,8 +566,11 @@ extern "C" int dbg_get_status(dbg_handle h, void *stream) {
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t st = 0;
+  unsigned long long spilled = 0;
   DBG_CK(cudaMemcpyAsync(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaMemcpyAsync(&spilled, h->d_spill_count, sizeof(spilled), cudaMemcpyDeviceToHost, s));
   DBG_CK(cudaStreamSynchronize(s));
+  if (st == DBG_OK && spilled > 0) return DBG_ERR_NEEDS_GROW;
   return (int)st;
 }
 
@@ -534,11 +583,14 @@ extern "C" int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, 
   if (st != DBG_OK) return st;
   unsigned long long acc[2] = {0, 0};
   uint32_t status = 0;
+  unsigned long long spilled = 0;
   DBG_CK(cudaMemcpyAsync(acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
   DBG_CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaMemcpyAsync(&spilled, h->d_spill_count, sizeof(spilled), cudaMemcpyDeviceToHost, s));
   DBG_CK(cudaStreamSynchronize(s));
   if (n_vertices) *n_vertices = acc[0];
   if (n_edges) *n_edges = acc[1];
+  if (status == DBG_OK && spilled > 0) return DBG_ERR_NEEDS_GROW;
   return (int)status;
 }
 
@@ -578,6 +630,7 @@ extern "C" const char *dbg_strerror(int code) {
     case DBG_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
     case DBG_ERR_BAD_OFFSETS: return "offsets are not non-decreasing";
     case DBG_ERR_NOALLOC_LIMIT: return "graph larger than the no-alloc export's fixed scratch";
+    case DBG_ERR_NEEDS_GROW: return "vertices were spilled: call dbg_grow to complete the graph";
     default: return "unknown status";
   }
 }

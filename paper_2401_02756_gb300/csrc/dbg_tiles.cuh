@@ -45,6 +45,9 @@ struct VertexCtx {
   uint32_t max_probes;
   int k;
   int item;
+  SpillRecord *spill;
+  uint64_t spill_cap;
+  unsigned long long *spill_count;
 };
 
 __device__ __forceinline__ uint4 ldg_stream_v4(const uint8_t *p) {
@@ -136,8 +139,9 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
     if (s_stop == 0u) {
       const uint8_t *packed = s_item.packed;
       const uint64_t origin = s_item.origin;
-      const VertexCtx ctx{s_item.table, s_item.n_slots, s_item.status, s_item.max_probes,
-                          s_item.k, s_item_idx};
+      const VertexCtx ctx{s_item.table,      s_item.n_slots,   s_item.status,
+                          s_item.max_probes, s_item.k,         s_item_idx,
+                          s_item.spill,      s_item.spill_cap, s_item.spill_count};
       const int k = ctx.k, m = k - 1;
       const uint64_t nbytes = s_nbytes;
       const int vec_ok = s_item.vec_ok;

@@ -19,19 +19,24 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdbg.so")
 
 (OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_BUFFER_TOO_SMALL, ERR_BAD_OFFSETS,
- ERR_NOALLOC_LIMIT) = range(8)
+ ERR_NOALLOC_LIMIT, ERR_NEEDS_GROW) = range(9)
 STATUS_NAMES = {0: "DBG_OK", 1: "DBG_ERR_INVALID_ARG", 2: "DBG_ERR_OOM", 3: "DBG_ERR_CAPACITY",
                 4: "DBG_ERR_CUDA", 5: "DBG_ERR_BUFFER_TOO_SMALL", 6: "DBG_ERR_BAD_OFFSETS",
-                7: "DBG_ERR_NOALLOC_LIMIT"}
+                7: "DBG_ERR_NOALLOC_LIMIT", 8: "DBG_ERR_NEEDS_GROW"}
 NOALLOC_EXPORT_MAX_VERTICES = 1 << 19
 
 EXPORTED = [
     "dbg_create", "dbg_create_ex", "dbg_destroy", "dbg_reset", "dbg_set_tuning", "dbg_get_info",
-    "dbg_reserve_events", "dbg_enable_kernel_timing", "dbg_kernel_times",
+    "dbg_reserve_events", "dbg_enable_kernel_timing", "dbg_kernel_times", "dbg_set_spill",
+    "dbg_grow",
     "dbg_insert_reads", "dbg_insert_reads_host", "dbg_insert_batch", "dbg_get_status", "dbg_stats",
     "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
-    "dbg_probe_random_sectors",
+    "dbg_probe_random_sectors", "dbg_probe_window", "dbg_sketch_reads", "dbg_sketch_estimate",
+    "dbg_mlp_work_floats", "dbg_mlp_features", "dbg_mlp_init", "dbg_mlp_forward",
+    "dbg_mlp_train_step",
 ]
+MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 1024, 64, 69825
+SKETCH_REGISTERS = 1024
 
 
 class DbgError(RuntimeError):
@@ -47,13 +52,15 @@ class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("tile_reads", ctypes.c_int),
                 ("grid_ctas", ctypes.c_int), ("warp_aggregate", ctypes.c_int),
                 ("insert_path", ctypes.c_int), ("apply_unroll", ctypes.c_int),
-                ("apply_counters", ctypes.c_int), ("region_log2", ctypes.c_int)]
+                ("apply_chunk", ctypes.c_int), ("apply_ctas", ctypes.c_int),
+                ("apply_counters", ctypes.c_int), ("region_log2", ctypes.c_int),
+                ("apply_group", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("n_slots", ctypes.c_uint64), ("table_bytes", ctypes.c_uint64),
                 ("max_probes", ctypes.c_uint32), ("device", ctypes.c_int),
-                ("event_capacity", ctypes.c_uint64)]
+                ("event_capacity", ctypes.c_uint64), ("spill_capacity", ctypes.c_uint64)]
 
 
 class BatchItem(ctypes.Structure):
@@ -82,6 +89,8 @@ def load() -> ctypes.CDLL:
         "dbg_set_tuning": (I, [P, ctypes.POINTER(Tuning)]),
         "dbg_get_info": (I, [P, ctypes.POINTER(Info)]),
         "dbg_reserve_events": (I, [P, U64]),
+        "dbg_set_spill": (I, [P, U64]),
+        "dbg_grow": (I, [P, U64, P]),
         "dbg_enable_kernel_timing": (I, [P, I]),
         "dbg_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(I)]),
         "dbg_insert_reads": (I, [P, P, P, U64, P]),
@@ -95,6 +104,14 @@ def load() -> ctypes.CDLL:
         "dbg_strerror": (ctypes.c_char_p, [I]),
         "dbg_last_cuda_error": (ctypes.c_char_p, []),
         "dbg_probe_random_sectors": (I, [P, U64, U64, U64, I, P]),
+        "dbg_probe_window": (I, [P, U64, U64, U64, U64, I, P]),
+        "dbg_sketch_reads": (I, [I, P, P, U64, P, P]),
+        "dbg_sketch_estimate": (ctypes.c_double, [P]),
+        "dbg_mlp_work_floats": (U64, [I]),
+        "dbg_mlp_features": (I, [P, ctypes.c_int64, I, P, P]),
+        "dbg_mlp_init": (I, [P, U64, P]),
+        "dbg_mlp_forward": (I, [P, P, I, P, P, P]),
+        "dbg_mlp_train_step": (I, [P, P, P, P, I, ctypes.c_float, P, P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -193,18 +210,27 @@ class Graph:
         _check(load().dbg_get_info(self.handle, ctypes.byref(inf)), "dbg_get_info")
         return {"k": inf.k, "n_slots": inf.n_slots, "table_bytes": inf.table_bytes,
                 "max_probes": inf.max_probes, "device": inf.device,
-                "event_capacity": inf.event_capacity}
+                "event_capacity": inf.event_capacity, "spill_capacity": inf.spill_capacity}
 
-    def set_tuning(self, block_threads: int = 0, tile_reads: int = 0, grid_ctas: int = 0,
-                   warp_aggregate: int = -1, insert_path: int = 0, apply_unroll: int = 0,
-                   apply_counters: int = 0, region_log2: int = 0) -> None:
-        """Launch shape and path of the insert (``insert_path``: 0 auto, 1 direct,
-        2 binned; ``apply_unroll``: binned apply events per thread, 4/8/16;
-        ``apply_counters``: binned apply work counters, 1..64; ``region_log2``:
-        binned table region of 2^n slots); the built graph does not depend on
-        any of these."""
-        t = Tuning(block_threads, tile_reads, grid_ctas, warp_aggregate, insert_path, apply_unroll,
-                   apply_counters, region_log2)
+    TUNING_FIELDS = ("block_threads", "tile_reads", "grid_ctas", "warp_aggregate", "insert_path",
+                     "apply_unroll", "apply_chunk", "apply_ctas", "apply_counters", "region_log2",
+                     "apply_group")
+
+    def set_tuning(self, **fields) -> None:
+        """Launch shape and path of the insert; fields (all optional, 0 = automatic):
+        ``block_threads``, ``tile_reads``, ``grid_ctas``, ``warp_aggregate`` (-1/0/1),
+        ``insert_path`` (1 direct, 2 binned), ``apply_unroll`` (2/4/8 probe slots per
+        thread), ``apply_chunk`` (4/8/16 events per thread per chunk), ``apply_ctas``
+        (CTAs per SM), ``apply_counters`` (1..64), ``region_log2`` (16..26),
+        ``apply_group`` (regions per apply launch).  The
+        built graph does not depend on any of these."""
+        unknown = set(fields) - set(self.TUNING_FIELDS)
+        if unknown:
+            raise ValueError(f"unknown tuning fields {sorted(unknown)}")
+        vals = {f: 0 for f in self.TUNING_FIELDS}
+        vals["warp_aggregate"] = -1
+        vals.update(fields)
+        t = Tuning(*[int(vals[f]) for f in self.TUNING_FIELDS])
         _check(load().dbg_set_tuning(self.handle, ctypes.byref(t)), "dbg_set_tuning")
 
     KERNELS = ("direct", "bin_count", "bin_scan", "bin_scatter", "bin_apply", "direct_fallback")
@@ -220,6 +246,16 @@ class Graph:
         _check(load().dbg_kernel_times(self.handle, buf, max_calls, ctypes.byref(n)),
                "dbg_kernel_times")
         return np.frombuffer(buf, dtype=np.float32)[: 6 * n.value].reshape(n.value, 6).copy()
+
+    def set_spill(self, records: int) -> None:
+        """Keep vertices that find no slot in a spill buffer of ``records``
+        records (0 removes it); complete the graph with :meth:`grow`."""
+        _check(load().dbg_set_spill(self.handle, int(records)), "dbg_set_spill")
+
+    def grow(self, new_capacity: int = 0, stream=None) -> None:
+        """Rebuild in a table of ``new_capacity`` slots (0: twice the size) and
+        replay the spilled vertices."""
+        _check(load().dbg_grow(self.handle, int(new_capacity), _stream(stream)), "dbg_grow")
 
     def reserve_events(self, events: int = 0) -> None:
         """Size the binned insert's event buffer (0 = default, 4 per slot)."""
@@ -298,6 +334,31 @@ def insert_batch(items, stream=None) -> None:
 def probe_random_sectors(buf, n_slots: int, n_ops: int, seed: int, mode: int, stream=None) -> None:
     _check(load().dbg_probe_random_sectors(_dptr(buf), int(n_slots), int(n_ops), int(seed),
                                            int(mode), _stream(stream)), "dbg_probe_random_sectors")
+
+
+def probe_window(buf, n_slots: int, n_ops: int, window_slots: int, seed: int, flags: int = 0,
+                 stream=None) -> None:
+    _check(load().dbg_probe_window(_dptr(buf), int(n_slots), int(n_ops), int(window_slots),
+                                   int(seed), int(flags), _stream(stream)), "dbg_probe_window")
+
+
+def sketch(k: int, packed, offsets, registers=None, stream=None):
+    """HyperLogLog registers of a read set's vertex keys (device tensors in,
+    a CUDA int32 tensor of SKETCH_REGISTERS + 1 words out; the last word is
+    the status)."""
+    import torch
+    if registers is None:
+        registers = torch.empty(SKETCH_REGISTERS + 1, dtype=torch.int32, device=packed.device)
+    _check(load().dbg_sketch_reads(int(k), _dptr(packed) or None, _dptr(offsets) or None,
+                                   int(offsets.numel()) - 1, _dptr(registers), _stream(stream)),
+           "dbg_sketch_reads")
+    return registers
+
+
+def sketch_estimate(registers) -> float:
+    """Distinct-key estimate from registers (host numpy array or CPU tensor)."""
+    r = np.ascontiguousarray(_host_view(registers, np.uint32)[:SKETCH_REGISTERS])
+    return float(load().dbg_sketch_estimate(r.ctypes.data))
 
 
 def pack_ascii(seq: str, phase: int = 0) -> np.ndarray:

@@ -89,3 +89,24 @@ def test_create_fails_loudly_without_a_gpu(lib):
     with pytest.raises(dbg.DbgError) as e:
         dbg.Graph(21, 1000)
     assert e.value.code in (dbg.ERR_CUDA, dbg.ERR_OOM)
+
+
+def _c_struct_fields(name):
+    txt = open(os.path.join(ROOT, "include", "dbg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    body = txt[txt.index(f"typedef struct {name} {{"):txt.index(f"}} {name};")]
+    return re.findall(r"\b(?:int|uint64_t|uint32_t)\s+(\w+)\s*;", body)
+
+
+def test_binding_structs_match_the_header(lib):
+    assert [f for f, _ in dbg.Tuning._fields_] == _c_struct_fields("dbg_tuning")
+    assert [f for f, _ in dbg.Info._fields_] == _c_struct_fields("dbg_info")
+    assert list(dbg.Graph.TUNING_FIELDS) == _c_struct_fields("dbg_tuning")
+
+
+def test_set_tuning_rejects_unknown_fields(lib):
+    class Fake(dbg.Graph):
+        def __init__(self):
+            self._h = None
+    with pytest.raises(ValueError):
+        Fake().set_tuning(no_such_field=1)

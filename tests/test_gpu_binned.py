@@ -136,3 +136,18 @@ def test_kernel_timer_records_the_kernels_each_path_launches():
             else:
                 assert (t[:, j] == -1).all(), (path, j, t)
         g.close()
+
+
+@pytest.mark.parametrize("tuning", [
+    dict(apply_unroll=2), dict(apply_unroll=8), dict(apply_chunk=4), dict(apply_chunk=16),
+    dict(apply_ctas=1), dict(apply_counters=1), dict(apply_counters=64),
+    dict(region_log2=16), dict(region_log2=26, apply_chunk=4, apply_unroll=2),
+])
+def test_binned_tuning_independence(tuning):
+    rs = synth.ragged_reads(2500, 250, 27, 40, lead=1)
+    g = binned_graph(rs, **tuning)
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert g.status() == dbg.OK
+    assert_same_graph(g.export(), oracle_export(rs))
+    g.close()

@@ -251,3 +251,32 @@ def test_invalid_arguments_rejected():
             oracle.build_graph(rs.packed, rs.offsets, k)
     with pytest.raises(RuntimeError):
         oracle.build_graph(rs.packed, np.array([4, 0], dtype=np.uint64), 3)
+
+
+# --------------------------------------------------------------------------
+# the sketch used to size tables (HyperLogLog of the vertex keys)
+# --------------------------------------------------------------------------
+
+def test_sketch_depends_only_on_the_distinct_keys():
+    rs = synth.ragged_reads(300, 150, 21, 901)
+    reads = [rs.read_ascii(r) for r in range(rs.n_reads)]
+    twice = synth.from_strings(reads + reads[::-1], 21, lead=3)
+    assert np.array_equal(oracle.sketch(rs.packed, rs.offsets, 21),
+                          oracle.sketch(twice.packed, twice.offsets, 21))
+
+
+def test_sketch_of_a_single_vertex():
+    rs = synth.from_strings(["A" * 60, "A" * 25], 21)  # every vertex is A^20
+    regs = oracle.sketch(rs.packed, rs.offsets, 21)
+    assert np.count_nonzero(regs) == 1 and 1 <= regs.max() <= 55
+    assert oracle.sketch(synth.from_strings(["ACG"], 21).packed,
+                         synth.from_strings(["ACG"], 21).offsets, 21).max() == 0
+
+
+@pytest.mark.parametrize("n,seed", [(40, 1), (600, 2), (6000, 3)])
+def test_sketch_estimate_within_the_hyperloglog_error(n, seed):
+    rs = synth.ragged_reads(n, 200, 25, 950 + seed)
+    D = oracle.build_graph(rs.packed, rs.offsets, 25).n_vertices
+    est = oracle.hll_estimate(oracle.sketch(rs.packed, rs.offsets, 25))
+    # standard error 1.04 / sqrt(1024) = 3.25 %; four of them
+    assert abs(est - D) <= 0.13 * D, (est, D)
