@@ -11,6 +11,10 @@ graph its own way (ASCII strings, a chained FNV-1a hash table, ``qsort``).
 * :func:`eulerian_path` / :func:`spell` -- Hierholzer's algorithm over the
   multigraph, backing the paper's statement that the assembly output is an
   Eulerian path over the graph (Section "Background").
+* ``oracle.contigs`` -- normalization (Section "Normalization of graph") and
+  contigs (Section "Finding contigs", Alg. 5), with the first flag that the C
+  builder keeps while inserting (``Graph.first``).
+* ``oracle.mlp`` -- the FP64 reference of the capacity predictor's network.
 
 Every function here is pinned by ``tests/test_oracle.py`` against values that
 do not come from the oracle itself (the Fig. 1 worked example, brute force,
@@ -63,6 +67,8 @@ def _load():
     lib.oracle_shard_of_keys.restype = None
     lib.oracle_sketch.argtypes = [P, P, U64, I, P]
     lib.oracle_sketch.restype = I
+    lib.oracle_export_first.argtypes = [P, P, U64]
+    lib.oracle_export_first.restype = I
     _lib = lib
     return lib
 
@@ -76,6 +82,7 @@ class Graph:
     keys: np.ndarray
     counts: np.ndarray
     strings: list[str] | None = None
+    first: np.ndarray | None = None  # uint8 [D]: no edge points to the vertex
 
     @property
     def n_vertices(self) -> int:
@@ -107,6 +114,10 @@ def build_graph(packed: np.ndarray, offsets: np.ndarray, k: int, *, shard_mod: i
         st = lib.oracle_export_sorted(g, keys.ctypes.data, counts.ctypes.data, n)
         if st != 0:
             raise RuntimeError(f"oracle_export_sorted failed with status {st}")
+        first = np.empty(n, dtype=np.uint8)
+        st = lib.oracle_export_first(g, first.ctypes.data if n else None, n) if n else 0
+        if st != 0:
+            raise RuntimeError(f"oracle_export_first failed with status {st}")
         strs = None
         if strings:
             m = k - 1
@@ -118,7 +129,7 @@ def build_graph(packed: np.ndarray, offsets: np.ndarray, k: int, *, shard_mod: i
             strs = [raw[i * m:(i + 1) * m] for i in range(n)]
     finally:
         lib.oracle_free(g)
-    return Graph(k, keys, counts, strs)
+    return Graph(k, keys, counts, strs, first)
 
 
 def shard_of_keys(keys: np.ndarray, k: int, shard_mod: int) -> np.ndarray:

@@ -96,6 +96,7 @@ static uint64_t encode(const char *s, int m) {
 typedef struct {
   uint64_t next; /* index + 1 of the next node in the chain, 0 = end */
   uint32_t cnt[4];
+  uint32_t first; /* Section "Finding contigs": no edge points to this vertex */
 } node_t;
 
 typedef struct {
@@ -141,12 +142,15 @@ static int vmap_rehash(vmap_t *v) {
 }
 
 /* Find the vertex with string s, adding it with zero counters if absent
- * (Alg. 4 "findVertex" followed by the insertion of Alg. 3).  Returns the
- * node index, or UINT64_MAX when memory runs out. */
-static uint64_t vmap_find_or_add(vmap_t *v, const char *s, uint64_t hash) {
+ * (Alg. 4 "findVertex" followed by the insertion of Alg. 3).  *created tells
+ * whether it was added.  Returns the node index, or UINT64_MAX when memory
+ * runs out. */
+static uint64_t vmap_find_or_add(vmap_t *v, const char *s, uint64_t hash, int *created) {
   uint64_t b = hash % v->nbuckets;
+  *created = 0;
   for (uint64_t i = v->head[b]; i != 0; i = v->nodes[i - 1].next)
     if (memcmp(v->strs + (i - 1) * (uint64_t)v->m, s, (size_t)v->m) == 0) return i - 1;
+  *created = 1;
   if (v->n == v->cap) {
     uint64_t nc = v->cap * 2;
     node_t *nn = (node_t *)realloc(v->nodes, nc * sizeof(node_t));
@@ -160,6 +164,7 @@ static uint64_t vmap_find_or_add(vmap_t *v, const char *s, uint64_t hash) {
   uint64_t idx = v->n++;
   memcpy(v->strs + idx * (uint64_t)v->m, s, (size_t)v->m);
   memset(v->nodes[idx].cnt, 0, sizeof(v->nodes[idx].cnt));
+  v->nodes[idx].first = 0;
   v->nodes[idx].next = v->head[b];
   v->head[b] = idx + 1;
   if (v->n > v->nbuckets) {
@@ -217,16 +222,20 @@ static void *build_worker(void *arg) {
       const char *right = buf + j + 1; /* s_1 .. s_{k-1} */
       char label = buf[j + (uint64_t)k - 1];
       uint64_t hl = fnv1a(left, m);
+      int created;
       if (owned(J, hl)) { /* addLeftVertex: find-or-add, then count the edge */
-        uint64_t v = vmap_find_or_add(J->map, left, hl);
+        uint64_t v = vmap_find_or_add(J->map, left, hl, &created);
         if (v == UINT64_MAX) { J->status = OR_ERR_NOMEM; free(buf); return NULL; }
         J->map->nodes[v].cnt[label_column(label)] += 1u;
+        /* a vertex created as a left vertex has no edge pointing to it yet */
+        if (created) J->map->nodes[v].first = 1u;
       }
       uint64_t hr = fnv1a(right, m);
-      if (owned(J, hr)) { /* addRightVertex: only make sure it exists */
-        if (vmap_find_or_add(J->map, right, hr) == UINT64_MAX) {
-          J->status = OR_ERR_NOMEM; free(buf); return NULL;
-        }
+      if (owned(J, hr)) { /* addRightVertex: make sure it exists; an edge now
+                             points to it, so its first flag is cleared */
+        uint64_t v = vmap_find_or_add(J->map, right, hr, &created);
+        if (v == UINT64_MAX) { J->status = OR_ERR_NOMEM; free(buf); return NULL; }
+        J->map->nodes[v].first = 0u;
       }
     }
   }
@@ -303,6 +312,7 @@ uint64_t oracle_num_vertices(const oracle_graph *g) {
 typedef struct {
   const char *s;
   const uint32_t *cnt;
+  uint32_t first;
 } ref_t;
 
 static int g_sort_m; /* string length for the comparator (export is single-threaded) */
@@ -320,6 +330,7 @@ static int sorted_refs(const oracle_graph *g, ref_t **out, uint64_t *n_out) {
     for (uint64_t i = 0; i < g->parts[p].n; ++i) {
       refs[j].s = g->parts[p].strs + i * (uint64_t)(g->k - 1);
       refs[j].cnt = g->parts[p].nodes[i].cnt;
+      refs[j].first = g->parts[p].nodes[i].first;
       ++j;
     }
   g_sort_m = g->k - 1;
@@ -342,6 +353,19 @@ int oracle_export_sorted(const oracle_graph *g, uint64_t *keys, uint32_t *counts
     if (keys) keys[i] = encode(refs[i].s, g->k - 1);
     if (counts) memcpy(counts + 4 * i, refs[i].cnt, 4 * sizeof(uint32_t));
   }
+  free(refs);
+  return OR_OK;
+}
+
+/* The same order: each vertex's first flag (1 = no edge points to it). */
+int oracle_export_first(const oracle_graph *g, uint8_t *out, uint64_t max_n) {
+  ref_t *refs;
+  uint64_t n;
+  if (!g || !out) return OR_ERR_ARG;
+  if (oracle_num_vertices(g) > max_n) return OR_ERR_ARG;
+  int st = sorted_refs(g, &refs, &n);
+  if (st != OR_OK) return st;
+  for (uint64_t i = 0; i < n; ++i) out[i] = (uint8_t)refs[i].first;
   free(refs);
   return OR_OK;
 }

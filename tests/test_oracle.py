@@ -280,3 +280,214 @@ def test_sketch_estimate_within_the_hyperloglog_error(n, seed):
     est = oracle.hll_estimate(oracle.sketch(rs.packed, rs.offsets, 25))
     # standard error 1.04 / sqrt(1024) = 3.25 %; four of them
     assert abs(est - D) <= 0.13 * D, (est, D)
+
+
+# --------------------------------------------------------------------------
+# the capacity predictor's network (FP64 reference)
+# --------------------------------------------------------------------------
+
+from oracle import mlp  # noqa: E402
+
+
+def _mlp_case(seed: int, batch: int, scale: float = 1.0):
+    rng = np.random.default_rng(seed)
+    blocks = {"W1": rng.uniform(-1, 1, (mlp.HID, mlp.IN)) * np.sqrt(6 / mlp.IN) * scale,
+              "b1": rng.normal(0, 0.1, mlp.HID), "W2": rng.uniform(-1, 1, (mlp.HID, mlp.HID))
+              * np.sqrt(6 / mlp.HID), "b2": rng.normal(0, 0.1, mlp.HID),
+              "w3": rng.uniform(-1, 1, mlp.HID) * np.sqrt(6 / mlp.HID), "b3": 0.3}
+    x = rng.integers(0, 25, (batch, mlp.IN)) / 64.0
+    t = rng.normal(12.0, 2.0, batch)
+    return mlp.pack(blocks), x, t
+
+
+def test_mlp_layout_round_trips():
+    p, _, _ = _mlp_case(1, 1)
+    assert p.size == mlp.N_PARAMS == 69825
+    assert np.array_equal(mlp.pack(mlp.unpack(p)), p)
+
+
+def test_mlp_single_path_closed_form():
+    # one unit per layer: y = w3 * relu(W2 * relu(W1 x0 + b1) + b2) + b3
+    q = {n: np.zeros_like(a) for n, a in mlp.unpack(np.zeros(mlp.N_PARAMS)).items()}
+    q["W1"][5, 7], q["b1"][5], q["W2"][9, 5], q["b2"][9], q["w3"][9], q["b3"] = 2, -1, 3, 0.5, 4, 0.25
+    x = np.zeros((3, mlp.IN))
+    x[:, 7] = [0.0, 0.75, 2.0]
+    y, _ = mlp.forward(mlp.pack(q), x)
+    expect = [4 * max(0.0, 3 * max(0.0, 2 * v - 1) + 0.5) + 0.25 for v in (0.0, 0.75, 2.0)]
+    assert np.allclose(y, expect, rtol=0, atol=1e-12)
+
+
+def test_mlp_zero_weights_gradient_is_the_bias_residual():
+    p = np.zeros(mlp.N_PARAMS)
+    p[-1] = 1.5
+    x = np.random.default_rng(2).random((5, mlp.IN))
+    t = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    l, g = mlp.loss_and_grads(p, x, t)
+    assert l == pytest.approx(0.5 * np.mean((1.5 - t) ** 2))
+    assert g[-1] == pytest.approx(np.mean(1.5 - t))
+    assert not np.any(g[:-1])
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_mlp_gradients_match_finite_differences(seed):
+    p, x, t = _mlp_case(seed, 7)
+    _, g = mlp.loss_and_grads(p, x, t)
+    rng = np.random.default_rng(seed)
+    # indices from every block (W1, b1, W2, b2, w3, b3)
+    bounds = np.cumsum([0, mlp.HID * mlp.IN, mlp.HID, mlp.HID * mlp.HID, mlp.HID, mlp.HID, 1])
+    idx = np.concatenate([rng.integers(bounds[i], bounds[i + 1], 12) for i in range(6)])
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mlp.loss(p + e, x, t) - mlp.loss(p - e, x, t)) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-7), i
+
+
+def test_adam_first_step_moves_each_parameter_by_lr():
+    # m_hat = g and v_hat = g^2 after one step, so the move is lr * g / (|g| + eps)
+    g = np.array([3.0, -0.5, 0.0, 1e-3])
+    p1, m, v = mlp.adam_step(np.ones(4), g, np.zeros(4), np.zeros(4), 1, 0.01)
+    assert np.allclose(p1, 1 - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+    # a constant gradient keeps m_hat / sqrt(v_hat) = sign(g) at every step
+    p, m, v = np.zeros(1), np.zeros(1), np.zeros(1)
+    for s in range(1, 6):
+        p, m, v = mlp.adam_step(p, np.array([2.0]), m, v, s, 0.1)
+    assert p[0] == pytest.approx(-0.5, rel=1e-8)
+
+
+def test_abs_forward_bounds_the_network():
+    p, x, _ = _mlp_case(5, 9)
+    y, _ = mlp.forward(p, x)
+    assert np.all(np.abs(y) <= mlp.abs_forward(p, x) + 1e-12)
+
+
+# --------------------------------------------------------------------------
+# the first flag, normalization and contigs (Section "Normalization of
+# graph", Section "Finding contigs", Alg. 5)
+# --------------------------------------------------------------------------
+
+from oracle import contigs as oc  # noqa: E402
+
+
+def load_contig_cases():
+    cases, cur = [], None
+    with open(os.path.join(GOLDEN, "contigs_k4.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("case "):
+                _, read, k = line.split()
+                cur = (read, int(k), [])
+                cases.append(cur)
+            else:
+                cur[2].append(line)
+    return cases
+
+
+def graph_of(reads, k):
+    rs = synth.from_strings(reads, k)
+    return oracle.build_graph(rs.packed, rs.offsets, k)
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_contigs_of_hand_worked_graphs(case):
+    read, k, expect = load_contig_cases()[case]
+    g = graph_of([read], k)
+    assert oc.find_contigs(g.keys, g.counts, k) == expect
+    assert oc.find_contigs(g.keys, g.counts, k, g.first) == expect
+
+
+def test_fig1_has_no_first_vertex():
+    g = graph_of(["ACGACGACGC"], 4)
+    assert not g.first.any()
+    g = graph_of(["GGACGTACGTA"], 4)
+    assert [oc.decode(key, 3) for key in g.keys[g.first.astype(bool)]] == ["GGA"]
+
+
+@pytest.mark.parametrize("k,seed", [(3, 1), (5, 2), (21, 3)])
+def test_first_flag_is_zero_in_degree(k, seed):
+    # the paper sets first on a vertex created as a left vertex and clears it
+    # whenever the vertex is a right vertex: whatever the order, it ends up
+    # set exactly on vertices that are no k-mer's suffix
+    rs = synth.ragged_reads(400, 60, k, 3100 + seed)
+    reads = [rs.read_ascii(r) for r in range(rs.n_reads)]
+    suffixes = {r[j + 1:j + k] for r in reads for j in range(len(r) - k + 1)}
+    g = oracle.build_graph(rs.packed, rs.offsets, k, strings=True)
+    for s, f in zip(g.strings, g.first):
+        assert bool(f) == (s not in suffixes)
+    assert np.array_equal(oc.first_flags(g.keys, g.counts, k), g.first)
+
+
+def test_tiled_error_free_genome_is_one_contig():
+    # error-free reads tiling a random genome with no repeated 20-mer: the
+    # graph is one path from the genome's first 20-mer, which is one contig
+    # spelling the genome
+    codes = synth.random_genome(5000, 77)
+    genome = synth.codes_to_ascii(codes)
+    k = 21
+    assert len({genome[i:i + k - 1] for i in range(len(genome) - k + 2)}) == len(genome) - k + 2
+    reads = [genome[s:s + 100] for s in range(0, len(genome) - 100 + 1, 37)] + [genome[-100:]]
+    g = graph_of(reads, k)
+    assert oc.find_contigs(g.keys, g.counts, k) == [genome]
+    assert g.first.sum() == 1
+
+
+@pytest.mark.parametrize("k,seed", [(4, 5), (7, 6), (15, 7)])
+def test_contig_walk_invariants(k, seed):
+    rs = synth.ragged_reads(300, 80, k, 3200 + seed)
+    g = oracle.build_graph(rs.packed, rs.offsets, k, strings=True)
+    cnt = {s: c for s, c in zip(g.strings, g.counts)}
+    first = {s: bool(f) for s, f in zip(g.strings, g.first)}
+
+    def outs(v):
+        return [b for i, b in enumerate("ACGT") if cnt[v][i] > 0]
+
+    starts = [(v, b) for v in sorted(cnt) if first[v] or len(outs(v)) != 1 for b in outs(v)]
+    got = oc.find_contigs(g.keys, g.counts, k)
+    assert len(got) == len(starts)
+    for c, (v, b) in zip(got, starts):
+        assert c[:k] == v + b                       # one contig per start edge, in order
+        vs = [c[i:i + k - 1] for i in range(len(c) - k + 2)]
+        for i in range(len(vs) - 1):                # a walk along edges
+            assert c[i + k - 1] in outs(vs[i])
+        for i in range(1, len(vs) - 1):             # interior: one exit, not repeated
+            assert len(outs(vs[i])) == 1 and vs[i] not in vs[:i]
+        last = vs[-1]                               # the end: a branch, a dead end or a repeat
+        assert len(outs(last)) != 1 or last in vs[:-1]
+
+
+def test_normalization_rounds_to_nearest():
+    # floor(c / 2.5 + 0.5) worked by hand for c = 0..10
+    c = np.arange(11, dtype=np.uint32).reshape(-1, 1)
+    assert oc.normalize(c, 2.5).ravel().tolist() == [0, 0, 1, 1, 2, 2, 2, 3, 3, 4, 4]
+    # the 10 kb workload: 1000 reads x (100 - 21 + 1) / 10000 = 8
+    rs = synth.workload_10kb()
+    assert oc.divisor(rs.n_edges(), 10_000) == 8.0
+    big = np.array([[2 ** 32 - 1, 7, 0, 1]], dtype=np.uint32)
+    assert oc.normalize(big, 0.5).tolist() == [[2 ** 32 - 1, 14, 0, 2]]
+
+
+def test_normalization_removes_errors_and_keeps_the_genome():
+    # 30x error-free tiling plus a few reads with one substitution each: the
+    # normalized graph has only the genome's edges, which spell one contig
+    codes = synth.random_genome(3000, 91)
+    genome = synth.codes_to_ascii(codes)
+    k = 25
+    reads = []
+    for rep in range(30):
+        reads += [genome[s:s + 150] for s in range(rep, len(genome) - 150 + 1, 30)]
+    reads.append(genome[-150:])
+    reads.append(genome[:150])
+    bad = list(genome[500:650])
+    bad[70] = "A" if bad[70] != "A" else "C"
+    reads.append("".join(bad))
+    rs = synth.from_strings(reads, k)
+    g = oracle.build_graph(rs.packed, rs.offsets, k)
+    norm = oc.normalize(g.counts, oc.divisor(rs.n_edges(), len(genome)))
+    assert not np.array_equal(norm > 0, g.counts > 0)  # the error's k-mers are gone
+    got = oc.find_contigs(g.keys, norm, k)
+    # the genome minus its thinly covered ends, in one piece
+    assert len(got) == 1 and got[0] in genome and len(got[0]) > len(genome) - 150
