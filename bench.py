@@ -46,6 +46,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="100mbp_30x_k31",
                     help="100mbp_30x_k31 | 5mbp_50x_k31 | 10kb_k21 | batch256")
+    ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: device memory budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
@@ -445,49 +448,77 @@ def run_reference(args):
 
 
 def run_batch(args):
-    """256 independent samples: one batched insert (dbg_insert_batch) against
-    one plain dbg_insert_reads per sample, both into freshly emptied tables
-    of 1.5x each sample's distinct vertices (counted by a pilot build)."""
+    """256 independent samples of uneven size, sized by the capacity predictor
+    (sketch of every sample, one batched network forward), then built three
+    ways into the same tables: one plain dbg_insert_reads per sample, one
+    dbg_insert_batch call, and a CUDA graph holding that call, replayed.  The
+    exact builder then judges the predictor: its error against each sample's
+    distinct-vertex count."""
     import torch
 
     from paper_2401_02756_gb300 import build as _build
     from paper_2401_02756_gb300 import dbg, synth
+    from paper_2401_02756_gb300.predictor import REG_STRIDE, CapacityPredictor
     _build.build()
     dbg.load()
     torch.cuda.set_device(0)
     t_gen = time.perf_counter()
     samples = synth.batch_samples(256, seed=4)
     t_gen = time.perf_counter() - t_gen
-    dev_in, graphs, edges = [], [], 0
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    dev_in, edges = [], 0
     for rs in samples:
         pk = torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda()
         of = torch.from_numpy(rs.offsets.view(np.int64).copy()).cuda()
-        touches = int(np.maximum(rs.lengths() - rs.k + 2, 0).sum())
-        pilot = dbg.Graph(rs.k, touches + 64)
-        pilot.set_tuning(insert_path=1)
-        pilot.insert(pk, of)
-        D, _ = pilot.stats()
-        pilot.close()
-        g = dbg.Graph(rs.k, int(math.ceil(1.5 * D)) + 64)
         dev_in.append((pk, of))
-        graphs.append(g)
         edges += rs.n_edges()
-    stream = torch.cuda.current_stream()
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # sizing: sketches and one batched forward, timed
+    pred = CapacityPredictor()
+    regs = torch.zeros(len(samples), REG_STRIDE, dtype=torch.int32, device="cuda")
+
+    sketch_items = [(rs.k, pk, of, regs[i]) for i, (rs, (pk, of)) in enumerate(zip(samples, dev_in))]
+
+    def size_all():
+        dbg.sketch_batch(sketch_items, stream=stream)
+        return pred.log_vertices(regs, len(samples), stream=stream)
+
+    size_ms = []
+    for i in range(args.warmup + args.steps):
+        a, b = ev(), ev()
+        a.record(stream)
+        size_all()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            size_ms.append(a.elapsed_time(b))
+    preds = pred.predict_registers(regs, len(samples))
+    graphs = [dbg.Graph(rs.k, pred.capacity(p)) for rs, p in zip(samples, preds)]
+    items = [(g, pk, of) for g, (pk, of) in zip(graphs, dev_in)]
 
     def reset_all():
         for g in graphs:
             g.reset(stream)
 
     def batched():
-        dbg.insert_batch([(g, pk, of) for g, (pk, of) in zip(graphs, dev_in)], stream)
+        dbg.insert_batch(items, stream)
 
     def plain():
         for g, (pk, of) in zip(graphs, dev_in):
             g.insert(pk, of, stream=stream)
 
+    reset_all()
+    batched()  # allocates the binned graphs' scratch before the capture
+    torch.cuda.synchronize()
+    cap_stream = torch.cuda.Stream()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=cap_stream):
+        dbg.insert_batch(items, cap_stream)
+    torch.cuda.synchronize()
+
     results = {}
-    for name, fn in (("batched", batched), ("per_sample", plain)):
+    for name, fn in (("batched_graph", cg.replay), ("batched", batched), ("per_sample", plain)):
         for _ in range(args.warmup):
             reset_all()
             fn()
@@ -504,20 +535,112 @@ def run_batch(args):
         for g in graphs:
             if g.status() != dbg.OK:
                 raise RuntimeError(f"{name}: build failed")
-    bm, pm = statistics.mean(results["batched"]), statistics.mean(results["per_sample"])
-    line = {
-        "metric": METRIC, "value": edges / (bm / 1e3), "unit": "edges/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": bm, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "batch256", "samples": len(samples), "edges": edges,
-                   "k": sorted({rs.k for rs in samples}), "generation_s": t_gen},
-        "per_sample_edges_per_s": edges / (pm / 1e3),
-        "batched_over_per_sample": pm / bm,
-        "batch_ms_p50": float(np.percentile(results["batched"], 50)),
-        "batch_ms_p99": float(np.percentile(results["batched"], 99)),
-    }
+    D = np.array([g.stats()[0] for g in graphs], dtype=np.float64)
+    mlp = np.array([p.mlp for p in preds])
+    hll = np.array([p.hll for p in preds])
     for g in graphs:
         g.close()
+    gm = statistics.mean(results["batched_graph"])
+    bm = statistics.mean(results["batched"])
+    pm = statistics.mean(results["per_sample"])
+    sm = statistics.mean(size_ms)
+
+    def err(est):
+        e = np.abs(est / D - 1.0)
+        return {"mean": float(e.mean()), "p99": float(np.quantile(e, 0.99)),
+                "max": float(e.max())}
+
+    line = {
+        "metric": METRIC, "value": edges / (gm / 1e3), "unit": "edges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": gm, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batch256", "samples": len(samples), "edges": edges,
+                   "k": sorted({rs.k for rs in samples}), "generation_s": t_gen,
+                   "sizing": "capacity predictor (margin x 1.5 x predicted vertices)",
+                   "l2": "tables emptied between steps; 256 tables total "
+                         f"{sum(pred.capacity(p) for p in preds) * 32 / 1e9:.1f} GB > L2"},
+        "batched_edges_per_s": edges / (bm / 1e3),
+        "per_sample_edges_per_s": edges / (pm / 1e3),
+        "graph_over_per_sample": pm / gm,
+        "batched_over_per_sample": pm / bm,
+        "sizing_ms": sm,
+        "batched_predicted_edges_per_s": edges / ((gm + sm) / 1e3),
+        "batch_ms_p50": float(np.percentile(results["batched_graph"], 50)),
+        "batch_ms_p99": float(np.percentile(results["batched_graph"], 99)),
+        "predictor_error": {"network": err(mlp), "hyperloglog": err(hll),
+                            "tables_overflowed": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """The request loop: Poisson arrivals of build requests drawn from the
+    batched-build size distribution, served by the continuous-batching loop
+    and, for comparison, one at a time with plain calls.  A step is one
+    closed-loop pass (every request present at the start) and gives the
+    throughput; one realtime pass of each server gives the latencies."""
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_2401_02756_gb300 import build as _build
+    from paper_2401_02756_gb300 import dbg, synth
+    from paper_2401_02756_gb300.predictor import CapacityPredictor
+    from paper_2401_02756_gb300.serve import BuildServer, Request, sequential
+    n, rate, seed = args.requests, args.rate, 31
+    t_gen = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        made = pool.map(synth.batch_sample_arrays, [(i, seed) for i in range(n)], chunksize=2)
+    t_gen = time.perf_counter() - t_gen
+    _build.build()
+    dbg.load()
+    torch.cuda.set_device(0)
+    arrivals = synth.poisson_arrivals(n, rate, seed)
+    reqs = []
+    for (i, k, packed, offsets, e), t in zip(made, arrivals):
+        pp = torch.empty(packed.size, dtype=torch.uint8, pin_memory=True)
+        pp.numpy()[:] = packed
+        po = torch.empty(offsets.size, dtype=torch.int64, pin_memory=True)
+        po.numpy()[:] = offsets.view(np.int64)
+        reqs.append(Request(i, k, pp.numpy(), po.numpy().view(np.uint64), float(t), e))
+    edges = sum(r.edges for r in reqs)
+    pred = CapacityPredictor()
+    srv = BuildServer(pred, budget_bytes=args.budget_gb * 1e9)
+    warm = reqs[:min(16, n)]
+    srv.run(warm, realtime=False)
+    sequential(warm, pred, realtime=False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    closed, closed_seq = [], []
+    for _ in range(args.steps):
+        closed.append(srv.run(reqs, realtime=False).summary())
+    for _ in range(max(1, min(args.steps, 2))):
+        closed_seq.append(sequential(reqs, pred, realtime=False).summary())
+    live = srv.run(reqs, realtime=True).summary()
+    live_seq = sequential(reqs, pred, realtime=True).summary()
+    clock_info = clocks.stop()
+    thr = statistics.mean(c["edges_per_s"] for c in closed)
+    thr_seq = statistics.mean(c["edges_per_s"] for c in closed_seq)
+    line = {
+        "metric": METRIC, "value": thr, "unit": "edges/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": 1, "ms_per_step": statistics.mean(c["wall_s"] for c in closed) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": f"serve_poisson{rate:g}", "requests": n, "edges": edges,
+                   "arrival_rate_per_s": rate, "budget_gb": args.budget_gb,
+                   "sizes": "batched-build distribution (genome 50 kb-2 Mbp, 10-60x, k 21/31)",
+                   "generation_s": t_gen, "answer": "sorted graph exported to host memory"},
+        "latency_ms_p50": live["latency_ms_p50"], "latency_ms_p99": live["latency_ms_p99"],
+        "build_latency_ms_p50": live["build_latency_ms_p50"],
+        "build_latency_ms_p99": live["build_latency_ms_p99"],
+        "realtime": live, "closed_loop": closed[-1],
+        "sequential": {"edges_per_s": thr_seq, "latency_ms_p50": live_seq["latency_ms_p50"],
+                       "latency_ms_p99": live_seq["latency_ms_p99"], "realtime": live_seq},
+        "server_over_sequential": thr / thr_seq,
+        "clocks": clock_info,
+    }
     print(json.dumps(line), flush=True)
 
 
@@ -573,6 +696,8 @@ def main():
         run_probe_sweep(window_only=args.window_sweep)
     elif args.workload == "batch256" and args.impl == "ours":
         run_batch(args)
+    elif args.workload == "serve" and args.impl == "ours":
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

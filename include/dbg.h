@@ -97,8 +97,27 @@ int dbg_create(int k, uint64_t capacity, dbg_handle *out);
  * (0 = default: min(n_slots, 8192)). */
 int dbg_create_ex(int k, uint64_t capacity, uint32_t max_probes, dbg_handle *out);
 
+/* Device bytes dbg_create_on needs for `capacity` slots: the slots (32 bytes
+ * each) followed by a 256-byte status block.  0 when capacity is 0 or too large. */
+uint64_t dbg_table_bytes(uint64_t capacity);
+
+/* As dbg_create_ex, but on caller-owned device memory `mem` (256-byte
+ * aligned, at least dbg_table_bytes(capacity) bytes) and without any
+ * allocation or synchronization: the table is initialized asynchronously on
+ * `stream`, so later work on other streams must be ordered after it.  This
+ * is how a request loop sizes and starts one table per request from its own
+ * memory pool without stalling the device.  The caller keeps `mem` alive
+ * until every stream that used the handle has passed its last call on it.
+ * No counterpart in the paper (whose table is one fixed allocation).
+ * Errors: INVALID_ARG (k, capacity, alignment, mem_bytes), OOM (host), CUDA. */
+int dbg_create_on(int k, uint64_t capacity, uint32_t max_probes, void *mem, uint64_t mem_bytes,
+                  void *stream, dbg_handle *out);
+
 /* Release the table and every buffer the handle owns.  Synchronizes the
- * device first.  NULL is ignored. */
+ * device first when the handle owns device memory (always for dbg_create;
+ * for dbg_create_on only after a spill buffer, host staging, binned scratch
+ * or a grow allocated some); otherwise frees host state only and does not
+ * wait.  NULL is ignored. */
 void dbg_destroy(dbg_handle h);
 
 /* Empty the graph (every slot EMPTY, every counter 0) and clear the sticky
@@ -181,8 +200,12 @@ typedef struct dbg_batch_item {
  * tile) work units from one index space.  Graphs that take the binned path
  * (see dbg_insert_reads) are inserted with it, one after another.  Every graph
  * must live on the current device; all work is on `stream`.  The result equals
- * one dbg_insert_reads per item.  Errors: INVALID_ARG, OOM, CUDA; sticky
- * errors are recorded in each item's own graph. */
+ * one dbg_insert_reads per item.  The call may be captured into a CUDA graph
+ * (cudaStreamBeginCapture on `stream`) once every binned graph's scratch
+ * exists (dbg_reserve_events, or one uncaptured call); replays of the graph
+ * must then not overlap other binned inserts into the same graphs.
+ * Errors: INVALID_ARG, OOM, CUDA; sticky errors are recorded in each item's
+ * own graph. */
 int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *stream);
 
 /* Grow-and-rebuild.  dbg_set_spill gives the graph a buffer of `records`
@@ -226,6 +249,38 @@ int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *strea
  * status (nothing exported when it is set). */
 int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, uint64_t max_n,
                       uint64_t *n_out, void *stream);
+
+/* Normalization (Section "Normalization of graph"): every counter c of the
+ * graph becomes floor(c / divisor + 0.5), computed in IEEE double and capped
+ * at 2^32 - 1.  The paper's divisor is the number of k-mer duplicates,
+ * reads * (read length - k + 1) / genome size (for reads of uneven length:
+ * the number of edges / genome size).  Rounding to the nearest integer is a
+ * reading: the paper's counters are integers, and the rounding lets an error
+ * k-mer seen once fall to 0.  In place, stream-ordered; waits for `stream`
+ * first to check the sticky status.  Errors: INVALID_ARG (divisor not
+ * positive and finite), the sticky status, CUDA. */
+int dbg_normalize(dbg_handle h, double divisor, void *stream);
+
+/* Contigs (Section "Finding contigs", Alg. 5 findContigs and makePath).  An
+ * outgoing edge is a label with a nonzero counter; the first flag (no edge
+ * points to the vertex) is taken from the counters as they are now.  Every
+ * vertex that is first or has not exactly one outgoing edge starts one
+ * contig per outgoing edge; a contig follows edges while the vertex it
+ * reaches has exactly one outgoing edge, and stops on reaching a vertex it
+ * has already visited, keeping the edge into it.  Contigs are ordered by
+ * (start vertex key, first label).
+ * Output: bases_out gets every contig's bases as ASCII A/C/G/T, back to
+ * back; offsets_out[i] .. offsets_out[i+1] delimits contig i (n + 1 entries,
+ * offsets_out[0] = 0).  Both may be host or device memory; *n_contigs and
+ * *n_bases always receive the sizes, and with too small or NULL buffers
+ * (max_contigs < n or max_bases < total) nothing else is written and
+ * DBG_ERR_BUFFER_TOO_SMALL is returned: a two-call size query.  Uses the
+ * slots' padding word as scratch and temporary device memory (freed before
+ * returning); synchronizes `stream`.  Errors: INVALID_ARG, the sticky status,
+ * BUFFER_TOO_SMALL, CAPACITY (a target vertex missing: an incomplete graph),
+ * CUDA. */
+int dbg_find_contigs(dbg_handle h, char *bases_out, uint64_t max_bases, uint64_t *offsets_out,
+                     uint64_t max_contigs, uint64_t *n_contigs, uint64_t *n_bases, void *stream);
 
 /* Fixed scratch of dbg_export_sorted_noalloc, and the largest graph it exports. */
 #define DBG_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -274,6 +329,23 @@ int dbg_export_sorted_noalloc(dbg_handle h, uint64_t *keys_out, uint32_t *counts
  * Errors: INVALID_ARG, CUDA. */
 int dbg_sketch_reads(int k, const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads,
                      uint32_t *registers, void *stream);
+
+/* One read set of a batched sketch: its reads (device, as for
+ * dbg_insert_reads) and its DBG_SKETCH_REGISTERS + 1 device words of output
+ * (the registers, then a status word). */
+typedef struct dbg_sketch_item {
+  int k;
+  const uint8_t *packed;
+  const uint64_t *offsets;
+  uint64_t n_reads;
+  uint32_t *registers;
+} dbg_sketch_item;
+
+/* dbg_sketch_reads for many read sets at once: one launch per up to 128
+ * items, whose CTAs take (item, read tile) work units from one index space.
+ * Each item's registers equal those dbg_sketch_reads gives it.  Asynchronous
+ * on `stream`.  Errors: INVALID_ARG (k, NULL pointers), CUDA. */
+int dbg_sketch_batch(const dbg_sketch_item *items, int n_items, void *stream);
 
 /* Host helper: the HyperLogLog estimate of the number of distinct keys from
  * DBG_SKETCH_REGISTERS registers in host memory (raw estimate with the

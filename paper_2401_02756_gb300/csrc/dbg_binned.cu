@@ -493,11 +493,6 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events) {
   return DBG_OK;
 }
 
-#define DBG_TRY(...)               \
-  do {                             \
-    const int st_ = (__VA_ARGS__); \
-    if (st_ != DBG_OK) return st_; \
-  } while (0)
 
 template <int B, int U, int M>
 int launch_apply(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int sms,
@@ -547,8 +542,13 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   pk.d[0] = it;
   const int sms = std::max(1, h->sm_count);
 
-  // binned calls on one handle share its scratch: order them
-  DBG_CK(cudaStreamWaitEvent(s, h->bin_done, 0));
+  // binned calls on one handle share its scratch: order them.  Inside a
+  // stream capture the captured calls are ordered by the stream itself, and
+  // an event recorded outside the capture may not be waited on.
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  DBG_CK(cudaStreamIsCapturing(s, &capture));
+  const bool capturing = capture != cudaStreamCaptureStatusNone;
+  if (!capturing) DBG_CK(cudaStreamWaitEvent(s, h->bin_done, 0));
   DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, geo.parts * sizeof(unsigned long long), s));
   timer_mark(h, call, 1, s);
@@ -589,7 +589,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   const int st = launch_insert(&it, 1, tiles, tuning, h->sm_count, s, mv.flag);
   if (st != DBG_OK) return st;
   timer_mark(h, call, 6, s);
-  DBG_CK(cudaEventRecord(h->bin_done, s));
+  if (!capturing) DBG_CK(cudaEventRecord(h->bin_done, s));
   return DBG_OK;
 }
 

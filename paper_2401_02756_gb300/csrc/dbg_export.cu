@@ -94,7 +94,7 @@ extern "C" int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *cou
   const size_t cb = align256(D * sizeof(uint4));
   const size_t total = 4 * kb + cb + 256 + align256(temp_bytes);
   char *buf = nullptr;
-  DBG_CK(cudaMallocAsync(reinterpret_cast<void **>(&buf), total, s));
+  DBG_TRY(scratch_alloc(reinterpret_cast<void **>(&buf), total, s));
   unsigned long long *keys_a = reinterpret_cast<unsigned long long *>(buf);
   unsigned long long *keys_b = reinterpret_cast<unsigned long long *>(buf + kb);
   unsigned long long *idx_a = reinterpret_cast<unsigned long long *>(buf + 2 * kb);

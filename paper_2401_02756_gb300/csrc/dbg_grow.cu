@@ -95,7 +95,10 @@ int launch_grow(dbg_handle h, uint64_t new_capacity, cudaStream_t s) {
     cudaFree(nt);
     return st != DBG_OK ? st : DBG_ERR_CAPACITY;
   }
-  cudaFree(h->table);
+  // the grown table is the handle's own even when the old one was the
+  // caller's (whose memory, holding the status block, stays in use)
+  if (h->owns_slots) cudaFree(h->table);
+  h->owns_slots = true;
   h->table = nt;
   h->n_slots = new_capacity;
   h->max_probes = probes;

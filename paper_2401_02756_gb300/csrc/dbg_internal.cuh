@@ -182,6 +182,8 @@ struct dbg_graph {
   uint32_t max_probes = 0;
   bool max_probes_auto = true;  // max_probes follows the table size
   dbg::Slot *table = nullptr;
+  bool owns_slots = true;               // table allocated by the handle (not dbg_create_on's)
+  bool owns_small = true;               // status block allocated by the handle
   uint32_t *d_status = nullptr;
   unsigned long long *d_acc = nullptr;  // [2]: vertices, edges (stats)
   unsigned long long *d_spill_count = nullptr;  // spilled vertex positions
@@ -225,7 +227,17 @@ void timer_mark(dbg_handle h, int call, int m, cudaStream_t s);
 
 // Error plumbing shared by the entry points (host side).
 int cuda_fail(cudaError_t e, const char *what);
+// Temporary device memory from the library's stream-ordered pool (free it
+// with cudaFreeAsync on a stream).
+int scratch_alloc(void **p, size_t bytes, cudaStream_t s);
 int launch_grow(dbg_handle h, uint64_t new_capacity, cudaStream_t s);
+
+// Propagate a non-OK status from a library call.
+#define DBG_TRY(...)               \
+  do {                             \
+    const int st_ = (__VA_ARGS__); \
+    if (st_ != DBG_OK) return st_; \
+  } while (0)
 
 #define DBG_CK(call)                                        \
   do {                                                      \

@@ -22,6 +22,16 @@ namespace {
 constexpr unsigned long long kSketchSalt = 0x9E3779B97F4A7C15ull;
 constexpr int kSketchRegs = DBG_SKETCH_REGISTERS;
 
+__device__ __forceinline__ void sketch_hash(uint64_t key, uint32_t &idx, uint32_t &rho) {
+  const uint64_t h = fmix64(key ^ kSketchSalt);
+  idx = (uint32_t)(h >> 54);
+  const uint64_t rest = h << 10;
+  rho = rest ? (uint32_t)__clzll(rest) + 1u : 55u;
+}
+
+// Registers in shared memory (one read set per launch).  A register only
+// grows, and after the first few thousand keys almost no key raises it, so
+// each key reads its register first and takes the atomic only to raise it.
 struct SketchVisitor {
   static constexpr bool kUniformRounds = false;
   uint32_t *s_reg;
@@ -30,11 +40,9 @@ struct SketchVisitor {
   __device__ void round_end() {}
   __device__ void vertex(bool valid, uint64_t key, bool, uint32_t, int, int, const VertexCtx &) {
     if (!valid) return;
-    const uint64_t h = fmix64(key ^ kSketchSalt);
-    const uint32_t idx = (uint32_t)(h >> 54);
-    const uint64_t rest = h << 10;
-    const uint32_t rho = rest ? (uint32_t)__clzll(rest) + 1u : 55u;
-    atomicMax(&s_reg[idx], rho);
+    uint32_t idx, rho;
+    sketch_hash(key, idx, rho);
+    if (rho > *reinterpret_cast<volatile uint32_t *>(&s_reg[idx])) atomicMax(&s_reg[idx], rho);
   }
 };
 
@@ -50,6 +58,44 @@ __global__ void __launch_bounds__(BLOCK)
   __syncthreads();
   for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK)
     if (s_reg[j]) atomicMax(&regs[j], s_reg[j]);
+}
+
+// Many read sets per launch.  Each CTA takes a contiguous range of tiles, so
+// it meets few item boundaries; it keeps shared-memory registers for the
+// item at hand and merges them into that item's global registers (carried in
+// the descriptor's table pointer) when its tiles of the item end.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_sketch_batch(const __grid_constant__ ItemPack<kBatchItems> pk, int tile_reads,
+                   uint64_t chunk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *s_reg = reinterpret_cast<uint32_t *>(smem + tile_smem_bytes(tile_reads));
+  for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK) s_reg[j] = 0u;
+  __syncthreads();
+  SketchVisitor vis{s_reg};
+  const uint64_t t1 = min(pk.total_tiles, (blockIdx.x + 1) * chunk);
+  for (uint64_t t = blockIdx.x * chunk; t < t1;) {
+    const int it = find_item(pk, t);
+    const uint64_t end = it + 1 < pk.n_items ? pk.d[it + 1].tile_begin : pk.total_tiles;
+    const uint64_t tb = min(t1, end);
+    for_each_vertex<BLOCK, kBatchItems, 8>(pk, tile_reads, smem, vis, t, tb, 1);
+    __syncthreads();
+    uint32_t *g = reinterpret_cast<uint32_t *>(pk.d[it].table);
+    for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK)
+      if (s_reg[j]) {
+        atomicMax(&g[j], s_reg[j]);
+        s_reg[j] = 0u;
+      }
+    __syncthreads();
+    t = tb;
+  }
+}
+
+// Every item's registers and status word := 0.
+__global__ void k_zero_registers(const __grid_constant__ ItemPack<kBatchItems> pk) {
+  const int i = blockIdx.x;
+  uint32_t *r = reinterpret_cast<uint32_t *>(pk.d[i].table);
+  for (int j = threadIdx.x; j <= kSketchRegs; j += blockDim.x) r[j] = 0u;
 }
 
 }  // namespace
@@ -87,6 +133,58 @@ extern "C" int dbg_sketch_reads(int k, const uint8_t *packed, const uint64_t *of
   const int grid = (int)std::min<uint64_t>(pk.total_tiles, (uint64_t)std::max(1, per_sm) * sms);
   k_sketch<B><<<grid, B, smem, s>>>(pk, tile_reads, registers);
   DBG_CK(cudaGetLastError());
+  return DBG_OK;
+}
+
+extern "C" int dbg_sketch_batch(const dbg_sketch_item *items, int n_items, void *stream) {
+  using namespace dbg;
+  if (n_items < 0 || (n_items > 0 && !items)) return DBG_ERR_INVALID_ARG;
+  for (int i = 0; i < n_items; ++i)
+    if (items[i].k < 2 || items[i].k > 32 || !items[i].registers ||
+        (items[i].n_reads > 0 && (!items[i].packed || !items[i].offsets)))
+      return DBG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  constexpr int B = 256;
+  const int tile_reads = B;
+  const size_t smem = tile_smem_bytes(tile_reads) + kSketchRegs * sizeof(uint32_t);
+  int dev = 0, sms = 0, per_sm = 0;
+  DBG_CK(cudaGetDevice(&dev));
+  DBG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (smem > 48 * 1024)
+    DBG_CK(cudaFuncSetAttribute(k_sketch_batch<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sketch_batch<B>, B, smem));
+  for (int first = 0; first < n_items; first += kBatchItems) {
+    const int cnt = std::min(kBatchItems, n_items - first);
+    ItemPack<kBatchItems> pk{};
+    pk.n_items = cnt;
+    uint64_t tiles = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const dbg_sketch_item &src = items[first + i];
+      ItemDesc &it = pk.d[i];
+      it.packed = src.packed;
+      it.offsets = src.offsets;
+      it.n_reads = src.n_reads;
+      it.origin = 0;
+      it.table = reinterpret_cast<Slot *>(src.registers);  // the item's registers
+      it.n_slots = 1;
+      it.status = src.registers + kSketchRegs;  // bad offsets are reported here
+      it.max_probes = 0;
+      it.k = src.k;
+      it.tile_begin = tiles;
+      it.vec_ok = ((uintptr_t)src.packed & 15u) == 0 ? 1 : 0;
+      tiles += (src.n_reads + tile_reads - 1) / tile_reads;
+    }
+    pk.total_tiles = tiles;
+    k_zero_registers<<<cnt, 256, 0, s>>>(pk);
+    DBG_CK(cudaGetLastError());
+    if (tiles == 0) continue;
+    const uint64_t slots = (uint64_t)std::max(1, per_sm) * sms;
+    const uint64_t chunk = (tiles + slots - 1) / slots;
+    const int grid = (int)((tiles + chunk - 1) / chunk);
+    k_sketch_batch<B><<<grid, B, smem, s>>>(pk, tile_reads, chunk);
+    DBG_CK(cudaGetLastError());
+  }
   return DBG_OK;
 }
 

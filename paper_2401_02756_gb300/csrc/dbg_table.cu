@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -18,6 +19,39 @@ int cuda_fail(cudaError_t e, const char *what) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
            cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? DBG_ERR_OOM : DBG_ERR_CUDA;
+}
+
+// Temporary device memory of the export and contig passes: a stream-ordered
+// pool per device, owned by the library, that keeps up to kScratchKeep
+// bytes across synchronisations (the default pool would give every byte
+// back at each one, so a loop of exports would map and unmap memory each
+// time).  Anything above that is released as usual.
+namespace {
+constexpr uint64_t kScratchKeep = 1ull << 30;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+int scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  DBG_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return DBG_ERR_INVALID_ARG;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      DBG_CK(cudaMemPoolCreate(&g_pools[dev], &props));
+      uint64_t keep = kScratchKeep;
+      DBG_CK(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    pool = g_pools[dev];
+  }
+  DBG_CK(cudaMallocFromPoolAsync(p, bytes, pool, s));
+  return DBG_OK;
 }
 
 namespace {
@@ -155,43 +189,74 @@ using dbg::DeviceGuard;
 // lifecycle
 // ---------------------------------------------------------------------------
 
-extern "C" int dbg_create_ex(int k, uint64_t capacity, uint32_t max_probes, dbg_handle *out) {
+namespace {
+
+// The host-staging stream and events of dbg_insert_reads_host, made on first use.
+int ensure_copy_stream(dbg_handle h) {
+  if (h->copy_stream) return DBG_OK;
+  DBG_CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i) {
+    DBG_CK(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
+    DBG_CK(cudaEventCreateWithFlags(&h->ev_consumed[i], cudaEventDisableTiming));
+  }
+  return DBG_OK;
+}
+
+int check_create_args(int k, uint64_t capacity, dbg_handle *out) {
   if (!out) return DBG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (k < 2 || k > 32 || capacity == 0 || capacity > (~0ull / sizeof(dbg::Slot)))
+  if (k < 2 || k > 32 || capacity == 0 || capacity > (~0ull / sizeof(dbg::Slot)) - 256)
     return DBG_ERR_INVALID_ARG;
+  return DBG_OK;
+}
+
+dbg_graph *new_graph(int k, uint64_t capacity, uint32_t max_probes) {
   dbg_graph *h = new (std::nothrow) dbg_graph();
-  if (!h) return DBG_ERR_OOM;
+  if (!h) return nullptr;
   h->k = k;
   h->n_slots = capacity;
   h->max_probes = max_probes ? max_probes
                              : (uint32_t)std::min<uint64_t>(capacity, dbg::kDefaultMaxProbes);
   h->max_probes_auto = max_probes == 0;
-  int st = DBG_OK;
+  return h;
+}
+
+int device_of(dbg_handle h) {
+  DBG_CK(cudaGetDevice(&h->device));
+  DBG_CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+  return DBG_OK;
+}
+
+void carve_small(dbg_handle h, void *small) {
+  h->d_status = static_cast<uint32_t *>(small);
+  h->d_acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 16);
+  h->d_spill_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 32);
+}
+
+constexpr uint64_t kSmallBytes = 64;   // status, stats accumulators, spill count
+constexpr uint64_t kOnMemTail = 256;   // the same block at the end of caller memory
+
+}  // namespace
+
+extern "C" int dbg_create_ex(int k, uint64_t capacity, uint32_t max_probes, dbg_handle *out) {
+  int st = check_create_args(k, capacity, out);
+  if (st != DBG_OK) return st;
+  dbg_graph *h = new_graph(k, capacity, max_probes);
+  if (!h) return DBG_ERR_OOM;
   do {
-    cudaError_t e = cudaGetDevice(&h->device);
-    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaGetDevice"); break; }
-    e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaDeviceGetAttribute"); break; }
-    e = cudaMalloc(&h->table, capacity * sizeof(dbg::Slot));
+    st = device_of(h);
+    if (st != DBG_OK) break;
+    cudaError_t e = cudaMalloc(&h->table, capacity * sizeof(dbg::Slot));
     if (e != cudaSuccess) { h->table = nullptr; st = dbg::cuda_fail(e, "cudaMalloc(table)"); break; }
     void *small = nullptr;
-    e = cudaMalloc(&small, 64);
+    e = cudaMalloc(&small, kSmallBytes);
     if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaMalloc(status)"); break; }
-    h->d_status = static_cast<uint32_t *>(small);
-    h->d_acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 16);
-    h->d_spill_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 32);
-    e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { st = dbg::cuda_fail(e, "cudaStreamCreate"); break; }
-    for (int i = 0; i < 2 && st == DBG_OK; ++i) {
-      e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_consumed[i], cudaEventDisableTiming);
-      if (e != cudaSuccess) st = dbg::cuda_fail(e, "cudaEventCreate");
-    }
+    carve_small(h, small);
+    st = ensure_copy_stream(h);
     if (st != DBG_OK) break;
     st = dbg::launch_table_init(h->table, h->n_slots, h->copy_stream);
     if (st != DBG_OK) break;
-    e = cudaMemsetAsync(h->d_status, 0, 64, h->copy_stream);
+    e = cudaMemsetAsync(h->d_status, 0, kSmallBytes, h->copy_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_stream);
     if (e != cudaSuccess) { st = dbg::cuda_fail(e, "table init"); break; }
   } while (0);
@@ -207,12 +272,47 @@ extern "C" int dbg_create(int k, uint64_t capacity, dbg_handle *out) {
   return dbg_create_ex(k, capacity, 0, out);
 }
 
+extern "C" uint64_t dbg_table_bytes(uint64_t capacity) {
+  if (capacity == 0 || capacity > (~0ull / sizeof(dbg::Slot)) - 256) return 0;
+  return capacity * sizeof(dbg::Slot) + kOnMemTail;
+}
+
+extern "C" int dbg_create_on(int k, uint64_t capacity, uint32_t max_probes, void *mem,
+                             uint64_t mem_bytes, void *stream, dbg_handle *out) {
+  int st = check_create_args(k, capacity, out);
+  if (st != DBG_OK) return st;
+  if (!mem || ((uintptr_t)mem & 255u) || mem_bytes < dbg_table_bytes(capacity))
+    return DBG_ERR_INVALID_ARG;
+  dbg_graph *h = new_graph(k, capacity, max_probes);
+  if (!h) return DBG_ERR_OOM;
+  h->owns_slots = h->owns_small = false;
+  h->table = static_cast<dbg::Slot *>(mem);
+  carve_small(h, static_cast<char *>(mem) + capacity * sizeof(dbg::Slot));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = device_of(h);
+  if (st == DBG_OK) st = dbg::launch_table_init(h->table, h->n_slots, s);
+  if (st == DBG_OK) {
+    cudaError_t e = cudaMemsetAsync(h->d_status, 0, kSmallBytes, s);
+    if (e != cudaSuccess) st = dbg::cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (st != DBG_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return DBG_OK;
+}
+
 extern "C" void dbg_destroy(dbg_handle h) {
   if (!h) return;
   DeviceGuard g(h->device);
-  cudaDeviceSynchronize();
-  cudaFree(h->table);
-  cudaFree(h->d_status);
+  // cudaFree waits for the device anyway; a handle on caller memory that
+  // allocated nothing itself frees only host state and does not wait
+  const bool owns_device_memory = h->owns_slots || h->owns_small || h->stage_packed[0] ||
+                                  h->stage_offsets[0] || h->bin_ev || h->bin_meta || h->d_spill;
+  if (owns_device_memory) cudaDeviceSynchronize();
+  if (h->owns_slots) cudaFree(h->table);
+  if (h->owns_small) cudaFree(h->d_status);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->stage_packed[i]);
     cudaFree(h->stage_offsets[i]);
@@ -414,6 +514,8 @@ constexpr uint64_t kStageBytes = 256ull << 20;   // otherwise: packed bytes per 
 constexpr uint64_t kStageReads = 1ull << 22;     // otherwise: reads per host chunk
 
 int grow_stage(dbg_handle h, uint64_t bytes, uint64_t reads) {
+  const int st = ensure_copy_stream(h);
+  if (st != DBG_OK) return st;
   if (bytes > h->stage_packed_bytes) {
     DBG_CK(cudaStreamSynchronize(h->copy_stream));
     DBG_CK(cudaDeviceSynchronize());

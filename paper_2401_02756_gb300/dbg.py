@@ -26,12 +26,13 @@ STATUS_NAMES = {0: "DBG_OK", 1: "DBG_ERR_INVALID_ARG", 2: "DBG_ERR_OOM", 3: "DBG
 NOALLOC_EXPORT_MAX_VERTICES = 1 << 19
 
 EXPORTED = [
-    "dbg_create", "dbg_create_ex", "dbg_destroy", "dbg_reset", "dbg_set_tuning", "dbg_get_info",
+    "dbg_create", "dbg_create_ex", "dbg_table_bytes", "dbg_create_on", "dbg_destroy", "dbg_reset", "dbg_set_tuning", "dbg_get_info",
     "dbg_reserve_events", "dbg_enable_kernel_timing", "dbg_kernel_times", "dbg_set_spill",
     "dbg_grow",
     "dbg_insert_reads", "dbg_insert_reads_host", "dbg_insert_batch", "dbg_get_status", "dbg_stats",
-    "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
-    "dbg_probe_random_sectors", "dbg_probe_window", "dbg_sketch_reads", "dbg_sketch_estimate",
+    "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_normalize", "dbg_find_contigs", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
+    "dbg_probe_random_sectors", "dbg_probe_window", "dbg_sketch_reads", "dbg_sketch_batch",
+    "dbg_sketch_estimate",
     "dbg_mlp_work_floats", "dbg_mlp_features", "dbg_mlp_init", "dbg_mlp_forward",
     "dbg_mlp_train_step",
 ]
@@ -63,6 +64,11 @@ class Info(ctypes.Structure):
                 ("event_capacity", ctypes.c_uint64), ("spill_capacity", ctypes.c_uint64)]
 
 
+class SketchItem(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("packed", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("n_reads", ctypes.c_uint64), ("registers", ctypes.c_void_p)]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_void_p), ("packed", ctypes.c_void_p),
                 ("offsets", ctypes.c_void_p), ("n_reads", ctypes.c_uint64)]
@@ -84,6 +90,8 @@ def load() -> ctypes.CDLL:
     sig = {
         "dbg_create": (I, [I, U64, ctypes.POINTER(P)]),
         "dbg_create_ex": (I, [I, U64, U32, ctypes.POINTER(P)]),
+        "dbg_table_bytes": (U64, [U64]),
+        "dbg_create_on": (I, [I, U64, U32, P, U64, P, ctypes.POINTER(P)]),
         "dbg_destroy": (None, [P]),
         "dbg_reset": (I, [P, P]),
         "dbg_set_tuning": (I, [P, ctypes.POINTER(Tuning)]),
@@ -100,6 +108,8 @@ def load() -> ctypes.CDLL:
         "dbg_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
         "dbg_export_sorted": (I, [P, P, P, U64, ctypes.POINTER(U64), P]),
         "dbg_export_sorted_noalloc": (I, [P, P, P, U64, ctypes.POINTER(U64), P]),
+        "dbg_normalize": (I, [P, ctypes.c_double, P]),
+        "dbg_find_contigs": (I, [P, P, U64, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
         "dbg_pack_ascii": (I, [ctypes.c_char_p, U64, P, I, ctypes.POINTER(U64)]),
         "dbg_strerror": (ctypes.c_char_p, [I]),
         "dbg_last_cuda_error": (ctypes.c_char_p, []),
@@ -107,6 +117,7 @@ def load() -> ctypes.CDLL:
         "dbg_probe_window": (I, [P, U64, U64, U64, U64, I, P]),
         "dbg_sketch_reads": (I, [I, P, P, U64, P, P]),
         "dbg_sketch_estimate": (ctypes.c_double, [P]),
+        "dbg_sketch_batch": (I, [P, I, P]),
         "dbg_mlp_work_floats": (U64, [I]),
         "dbg_mlp_features": (I, [P, ctypes.c_int64, I, P, P]),
         "dbg_mlp_init": (I, [P, U64, P]),
@@ -173,10 +184,25 @@ def _host_view(x, dtype):
 class Graph:
     """An A-Bruijn graph under construction, held in device memory."""
 
-    def __init__(self, k: int, capacity: int, max_probes: int = 0):
+    def __init__(self, k: int, capacity: int, max_probes: int = 0, memory=None, stream=None):
+        """A table of ``capacity`` slots, allocated by the library, or -- when
+        ``memory`` (a CUDA uint8 tensor of at least ``table_bytes(capacity)``
+        bytes, 256-byte aligned) is given -- laid out in that memory and
+        initialized asynchronously on ``stream``.  The graph keeps a reference
+        to ``memory``; a caller that uses the graph on other streams than the
+        one ``memory`` was allocated on orders the release itself
+        (``Tensor.record_stream``)."""
         L = load()
         h = ctypes.c_void_p()
-        _check(L.dbg_create_ex(int(k), int(capacity), int(max_probes), ctypes.byref(h)), "dbg_create")
+        self._memory = None
+        if memory is None:
+            _check(L.dbg_create_ex(int(k), int(capacity), int(max_probes), ctypes.byref(h)),
+                   "dbg_create")
+        else:
+            _check(L.dbg_create_on(int(k), int(capacity), int(max_probes), _dptr(memory),
+                                   int(memory.numel() * memory.element_size()), _stream(stream),
+                                   ctypes.byref(h)), "dbg_create_on")
+            self._memory = memory
         self._h = h
         self.k = int(k)
 
@@ -191,6 +217,7 @@ class Graph:
         if getattr(self, "_h", None) is not None:
             load().dbg_destroy(self._h)
             self._h = None
+        self._memory = None
 
     def __del__(self):
         try:
@@ -291,10 +318,21 @@ class Graph:
                "dbg_stats")
         return int(nv.value), int(ne.value)
 
-    def export(self, stream=None) -> tuple[np.ndarray, np.ndarray]:
-        """Sorted vertices: keys (uint64 [D]) and counters (uint32 [D, 4], A C G T)."""
+    def export(self, stream=None, out=None) -> tuple[np.ndarray, np.ndarray]:
+        """Sorted vertices: keys (uint64 [D]) and counters (uint32 [D, 4], A C G T).
+        ``out`` = (keys, counts) host arrays (pinned for speed) of at least D
+        rows makes it one call into them; the views [:D] are returned."""
         L = load()
         n = ctypes.c_uint64()
+        if out is not None:
+            keys, counts = out
+            st = L.dbg_export_sorted(self.handle, keys.ctypes.data, counts.ctypes.data,
+                                     min(keys.shape[0], counts.shape[0]), ctypes.byref(n),
+                                     _stream(stream))
+            if st == OK:
+                return keys[:n.value], counts[:n.value]
+            if st != ERR_BUFFER_TOO_SMALL:
+                raise DbgError(st, "dbg_export_sorted")
         st = L.dbg_export_sorted(self.handle, None, None, 0, ctypes.byref(n), _stream(stream))
         if st not in (OK, ERR_BUFFER_TOO_SMALL):
             raise DbgError(st, "dbg_export_sorted")
@@ -305,6 +343,29 @@ class Graph:
             _check(L.dbg_export_sorted(self.handle, keys.ctypes.data, counts.ctypes.data, D,
                                        ctypes.byref(n), _stream(stream)), "dbg_export_sorted")
         return keys, counts
+
+    def normalize(self, divisor: float, stream=None) -> None:
+        """Counters := floor(counter / divisor + 0.5) (the paper's normalization)."""
+        _check(load().dbg_normalize(self.handle, float(divisor), _stream(stream)),
+               "dbg_normalize")
+
+    def contigs(self, stream=None) -> list[str]:
+        """The graph's contigs (Alg. 5), ordered by (start vertex, label)."""
+        L = load()
+        n, b = ctypes.c_uint64(), ctypes.c_uint64()
+        st = L.dbg_find_contigs(self.handle, None, 0, None, 0, ctypes.byref(n), ctypes.byref(b),
+                                _stream(stream))
+        if st not in (OK, ERR_BUFFER_TOO_SMALL):
+            raise DbgError(st, "dbg_find_contigs")
+        if n.value == 0:
+            return []
+        bases = np.empty(b.value, dtype=np.uint8)
+        offs = np.empty(n.value + 1, dtype=np.uint64)
+        _check(L.dbg_find_contigs(self.handle, bases.ctypes.data, bases.size, offs.ctypes.data,
+                                  n.value, ctypes.byref(n), ctypes.byref(b), _stream(stream)),
+               "dbg_find_contigs")
+        raw = bases.tobytes().decode("ascii")
+        return [raw[int(offs[i]):int(offs[i + 1])] for i in range(n.value)]
 
     def export_device(self, stream=None):
         """Sorted vertices as CUDA tensors (int64 keys [D], int32 counters [D, 4])."""
@@ -355,10 +416,63 @@ def sketch(k: int, packed, offsets, registers=None, stream=None):
     return registers
 
 
+def sketch_batch(items, stream=None) -> None:
+    """``items``: list of ``(k, packed, offsets, registers)`` device tensors;
+    each ``registers`` holds SKETCH_REGISTERS + 1 int32 words."""
+    arr = (SketchItem * max(1, len(items)))()
+    for i, (k, pk, of, rg) in enumerate(items):
+        arr[i] = SketchItem(int(k), _dptr(pk) or None, _dptr(of) or None, int(of.numel()) - 1,
+                            _dptr(rg))
+    _check(load().dbg_sketch_batch(arr, len(items), _stream(stream)), "dbg_sketch_batch")
+
+
 def sketch_estimate(registers) -> float:
     """Distinct-key estimate from registers (host numpy array or CPU tensor)."""
     r = np.ascontiguousarray(_host_view(registers, np.uint32)[:SKETCH_REGISTERS])
     return float(load().dbg_sketch_estimate(r.ctypes.data))
+
+
+def table_bytes(capacity: int) -> int:
+    """Device bytes a table of ``capacity`` slots takes on caller memory."""
+    return int(load().dbg_table_bytes(int(capacity)))
+
+
+def mlp_work_floats(batch: int) -> int:
+    """Floats of scratch the network needs for a batch."""
+    return int(load().dbg_mlp_work_floats(int(batch)))
+
+
+def mlp_features(registers, x, batch: int, stride: int | None = None, stream=None):
+    """x[b] = registers[b * stride : b * stride + MLP_INPUTS] / 64 (device tensors)."""
+    stride = SKETCH_REGISTERS + 1 if stride is None else int(stride)
+    _check(load().dbg_mlp_features(_dptr(registers), stride, int(batch), _dptr(x),
+                                   _stream(stream)), "dbg_mlp_features")
+    return x
+
+
+def mlp_init(params, seed: int, stream=None):
+    """He-uniform weights, zero biases, into a device float32 tensor of MLP_PARAMS."""
+    _check(load().dbg_mlp_init(_dptr(params), int(seed), _stream(stream)), "dbg_mlp_init")
+    return params
+
+
+def mlp_forward(params, x, y, work, batch: int | None = None, stream=None):
+    """y[b] = network(x[b]) (device float32 tensors; x is batch x MLP_INPUTS)."""
+    batch = int(y.numel()) if batch is None else int(batch)
+    _check(load().dbg_mlp_forward(_dptr(params), _dptr(x), batch, _dptr(y), _dptr(work),
+                                  _stream(stream)), "dbg_mlp_forward")
+    return y
+
+
+def mlp_train_step(params, grads, adam_m, adam_v, step: int, lr: float, x, target, work,
+                   loss=None, batch: int | None = None, stream=None):
+    """One Adam step on the mean of (y - target)^2 / 2; ``loss`` (a device
+    float32 tensor of one element, or None) receives the loss before the step."""
+    batch = int(target.numel()) if batch is None else int(batch)
+    _check(load().dbg_mlp_train_step(_dptr(params), _dptr(grads), _dptr(adam_m), _dptr(adam_v),
+                                     int(step), float(lr), _dptr(x), _dptr(target), batch,
+                                     _dptr(work), _dptr(loss) if loss is not None else None,
+                                     _stream(stream)), "dbg_mlp_train_step")
 
 
 def pack_ascii(seq: str, phase: int = 0) -> np.ndarray:

@@ -43,7 +43,7 @@ BASES = "ACGT"
 
 # stream identifiers (one per purpose so that draws never overlap)
 S_GENOME, S_START, S_ERRPOS, S_ERRVAL, S_LEN, S_FAMILY, S_COPYPOS, S_MUTPOS, \
-    S_MUTVAL, S_SEGMENT, S_SAMPLE = range(1, 12)
+    S_MUTVAL, S_SEGMENT, S_SAMPLE, S_ARRIVAL = range(1, 13)
 
 
 def splitmix64(z: np.ndarray) -> np.ndarray:
@@ -316,24 +316,42 @@ def workload_100mbp(seed: int = 3) -> ReadSet:
     return rs
 
 
-def batch_samples(n_samples: int = 256, seed: int = 4, gmin: float = 5e4, gmax: float = 2e6,
-                  cov_lo: float = 10.0, cov_hi: float = 60.0, read_len: int = 150,
-                  error_rate: float = 0.005, ks=(21, 31)) -> list[ReadSet]:
-    """Independent samples for the batched build: genome size log-uniform in
-    ``[gmin, gmax]``, coverage uniform in ``[cov_lo, cov_hi]``, k drawn from ``ks``."""
-    u = uniform01(draws(seed, S_SAMPLE, 3 * n_samples)).reshape(n_samples, 3)
-    out = []
-    for i in range(n_samples):
-        G = int(round(math.exp(math.log(gmin) + u[i, 0] * (math.log(gmax) - math.log(gmin)))))
-        cov = cov_lo + u[i, 1] * (cov_hi - cov_lo)
-        k = ks[min(len(ks) - 1, int(u[i, 2] * len(ks)))]
-        n = max(1, int(round(cov * G / read_len)))
-        s = seed * 100_003 + i
-        g = random_genome(G, s)
-        rs = sample_reads(g, n, read_len, error_rate, s, k, f"sample{i}")
-        rs.meta.update({"coverage": cov})
-        out.append(rs)
-    return out
+def batch_sample(i: int, seed: int = 4, gmin: float = 5e4, gmax: float = 2e6,
+                 cov_lo: float = 10.0, cov_hi: float = 60.0, read_len: int = 150,
+                 error_rate: float = 0.005, ks=(21, 31)) -> ReadSet:
+    """Sample ``i`` of the batched-build distribution: genome size log-uniform
+    in ``[gmin, gmax]``, coverage uniform in ``[cov_lo, cov_hi]``, k drawn
+    from ``ks``.  Each sample is a function of (seed, i) alone."""
+    u = uniform01(draws(seed, S_SAMPLE, 3, start=3 * i))
+    G = int(round(math.exp(math.log(gmin) + u[0] * (math.log(gmax) - math.log(gmin)))))
+    cov = cov_lo + u[1] * (cov_hi - cov_lo)
+    k = ks[min(len(ks) - 1, int(u[2] * len(ks)))]
+    n = max(1, int(round(cov * G / read_len)))
+    s = seed * 100_003 + i
+    g = random_genome(G, s)
+    rs = sample_reads(g, n, read_len, error_rate, s, k, f"sample{i}")
+    rs.meta.update({"coverage": cov})
+    return rs
+
+
+def batch_sample_arrays(job: tuple) -> tuple:
+    """(i, seed[, kwargs]) -> (i, k, packed, offsets, edges) of :func:`batch_sample`:
+    a picklable form for worker processes."""
+    i, seed = job[0], job[1]
+    rs = batch_sample(i, seed, **(job[2] if len(job) > 2 else {}))
+    return i, rs.k, rs.packed, rs.offsets, rs.n_edges()
+
+
+def batch_samples(n_samples: int = 256, seed: int = 4, **kw) -> list[ReadSet]:
+    """Samples 0 .. n_samples-1 of :func:`batch_sample`."""
+    return [batch_sample(i, seed, **kw) for i in range(n_samples)]
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of ``n`` requests of a Poisson process with the
+    given rate: cumulative sums of exponential gaps -ln(1 - u) / rate."""
+    u = uniform01(draws(seed, S_ARRIVAL, n))
+    return np.cumsum(-np.log1p(-u) / rate)
 
 
 WORKLOADS = {

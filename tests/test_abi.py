@@ -79,7 +79,27 @@ def test_argument_errors_return_before_any_launch(lib):
     n = ctypes.c_uint64()
     assert lib.dbg_export_sorted(None, None, None, 0, ctypes.byref(n), None) == dbg.ERR_INVALID_ARG
     assert lib.dbg_probe_random_sectors(None, 1, 1, 0, 0, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_sketch_reads(1, None, None, 0, None, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_sketch_estimate(None) < 0
+    assert lib.dbg_mlp_work_floats(0) == 0
+    assert lib.dbg_mlp_work_floats(3) == 3 * (4 * dbg.MLP_HIDDEN + 2) + 1
+    assert lib.dbg_mlp_features(None, 1025, 1, None, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_mlp_features(1, 1000, 1, 1, None) == dbg.ERR_INVALID_ARG  # stride < inputs
+    assert lib.dbg_mlp_init(None, 0, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_mlp_forward(1, 1, 0, 1, 1, None) == dbg.ERR_INVALID_ARG  # empty batch
+    assert lib.dbg_mlp_train_step(1, 1, 1, 1, 0, 1e-3, 1, 1, 4, 1, None, None) == \
+        dbg.ERR_INVALID_ARG  # step 0
+    assert lib.dbg_mlp_train_step(1, 1, 1, 1, 1, 0.0, 1, 1, 4, 1, None, None) == \
+        dbg.ERR_INVALID_ARG  # lr 0
     lib.dbg_destroy(None)
+
+
+def test_mlp_constants_match_the_reference_layout():
+    from oracle import mlp
+    assert (dbg.MLP_INPUTS, dbg.MLP_HIDDEN, dbg.MLP_PARAMS) == (mlp.IN, mlp.HID, mlp.N_PARAMS)
+    txt = open(os.path.join(ROOT, "include", "dbg.h")).read()
+    for name, v in (("INPUTS", mlp.IN), ("HIDDEN", mlp.HID), ("PARAMS", mlp.N_PARAMS)):
+        assert re.search(rf"#define DBG_MLP_{name} {v}\b", txt)
 
 
 def test_create_fails_loudly_without_a_gpu(lib):
@@ -95,13 +115,22 @@ def _c_struct_fields(name):
     txt = open(os.path.join(ROOT, "include", "dbg.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     body = txt[txt.index(f"typedef struct {name} {{"):txt.index(f"}} {name};")]
-    return re.findall(r"\b(?:int|uint64_t|uint32_t)\s+(\w+)\s*;", body)
+    return re.findall(r"\b(?:int|uint64_t|uint32_t|dbg_handle)\s*\**\s*(\w+)\s*;", body)
+
+
+def _c_struct_all_fields(name):
+    txt = open(os.path.join(ROOT, "include", "dbg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    body = txt[txt.index(f"typedef struct {name} {{"):txt.index(f"}} {name};")]
+    return re.findall(r"(\w+)\s*;", body)
 
 
 def test_binding_structs_match_the_header(lib):
     assert [f for f, _ in dbg.Tuning._fields_] == _c_struct_fields("dbg_tuning")
     assert [f for f, _ in dbg.Info._fields_] == _c_struct_fields("dbg_info")
     assert list(dbg.Graph.TUNING_FIELDS) == _c_struct_fields("dbg_tuning")
+    assert [f for f, _ in dbg.SketchItem._fields_] == _c_struct_all_fields("dbg_sketch_item")
+    assert len(dbg.BatchItem._fields_) == len(_c_struct_all_fields("dbg_batch_item"))
 
 
 def test_set_tuning_rejects_unknown_fields(lib):

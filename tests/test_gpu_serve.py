@@ -1,0 +1,158 @@
+"""The request loop: every exported graph is bit-identical whether its request
+is served alone or in a mix with others, matches the oracle, stays within
+the memory budget, and survives an under-predicted table exactly."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_02756_gb300 import build, dbg, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+    dbg.load()
+
+
+def requests(n, seed=41, gmax=2e5, rate=200.0):
+    from paper_2401_02756_gb300.serve import Request
+    arr = synth.poisson_arrivals(n, rate, seed)
+    out = []
+    for i in range(n):
+        rs = synth.batch_sample(i, seed, gmax=gmax)
+        out.append(Request(i, rs.k, rs.packed, rs.offsets, float(arr[i]), rs.n_edges()))
+    return out
+
+
+class Sink:
+    def __init__(self):
+        self.graphs = {}
+
+    def __call__(self, req, keys, counts):
+        assert req.rid not in self.graphs
+        self.graphs[req.rid] = (keys.copy(), counts.copy())
+
+
+@pytest.fixture(scope="module")
+def reqs():
+    return requests(14)
+
+
+@pytest.fixture(scope="module")
+def alone(reqs):
+    from paper_2401_02756_gb300.serve import BuildServer
+    srv = BuildServer(budget_bytes=40e9)
+    out = {}
+    for r in reqs:
+        sink = Sink()
+        srv.run([r], sink=sink, realtime=False)
+        out[r.rid] = sink.graphs[r.rid]
+    return out
+
+
+def assert_same(a, b):
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_alone_matches_the_oracle(reqs, alone):
+    for r in reqs[:4]:
+        g = oracle.build_graph(r.packed, r.offsets, r.k)
+        assert_same(alone[r.rid], (g.keys, g.counts))
+
+
+def test_mix_equals_alone_all_at_once(reqs, alone):
+    from paper_2401_02756_gb300.serve import BuildServer
+    sink = Sink()
+    rep = BuildServer(budget_bytes=40e9).run(reqs, sink=sink, realtime=False)
+    assert set(sink.graphs) == {r.rid for r in reqs}
+    for r in reqs:
+        assert_same(sink.graphs[r.rid], alone[r.rid])
+    s = rep.summary()
+    assert s["edges"] == sum(r.edges for r in reqs)
+    assert max(rep.batch_sizes) > 1  # requests really shared a batched insert
+
+
+def test_mix_equals_alone_with_poisson_arrivals(reqs, alone):
+    from paper_2401_02756_gb300.serve import BuildServer
+    sink = Sink()
+    rep = BuildServer(budget_bytes=40e9).run(reqs, sink=sink, realtime=True)
+    for r in reqs:
+        assert_same(sink.graphs[r.rid], alone[r.rid])
+    for t in rep.timings:
+        assert t.arrival <= t.admitted <= t.built <= t.done
+    s = rep.summary()
+    assert 0 < s["latency_ms_p50"] <= s["latency_ms_p99"]
+
+
+def test_tight_budget_queues_but_stays_within_it(reqs, alone):
+    from gpu_util import to_device
+    from paper_2401_02756_gb300 import predictor
+    from paper_2401_02756_gb300.serve import BuildServer, _round
+    pred = predictor.CapacityPredictor()
+    # each request's admitted footprint, as the server will compute it
+    need = []
+    for r in reqs:
+        rs = synth.ReadSet("r", r.k, r.packed, r.offsets)
+        cap = pred.capacity(pred.predict(r.k, *to_device(rs)))
+        need.append(r.input_bytes() + _round(dbg.table_bytes(cap)))
+    budget = 2 * max(need)  # room for about two of the largest at a time
+    assert budget < sum(need) / 2
+    sink = Sink()
+    rep = BuildServer(pred, budget_bytes=budget).run(reqs, sink=sink, realtime=False)
+    assert rep.peak_bytes <= budget
+    assert rep.batches > 2
+    for r in reqs:
+        assert_same(sink.graphs[r.rid], alone[r.rid])
+
+
+def test_under_predicted_tables_are_rebuilt_exactly(reqs, alone):
+    from paper_2401_02756_gb300.predictor import CapacityPredictor
+    from paper_2401_02756_gb300.serve import BuildServer
+    small = CapacityPredictor(margin=0.25)  # tables far too small: every build overflows
+    sink = Sink()
+    rep = BuildServer(small, budget_bytes=40e9).run(reqs[:6], sink=sink, realtime=False)
+    assert all(t.rebuilds >= 1 for t in rep.timings)
+    for r in reqs[:6]:
+        assert_same(sink.graphs[r.rid], alone[r.rid])
+
+
+def test_sequential_baseline_gives_the_same_graphs(reqs, alone):
+    from paper_2401_02756_gb300.predictor import CapacityPredictor
+    from paper_2401_02756_gb300.serve import sequential
+    sink = Sink()
+    rep = sequential(reqs[:5], CapacityPredictor(), sink=sink, realtime=False)
+    assert len(rep.timings) == 5
+    for r in reqs[:5]:
+        assert_same(sink.graphs[r.rid], alone[r.rid])
+
+
+def test_caller_memory_tables_match_library_tables():
+    import torch
+    rs = synth.ragged_reads(2000, 300, 31, 4242)
+    packed = torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda()
+    offsets = torch.from_numpy(rs.offsets.view(np.int64)).cuda()
+    from gpu_util import capacity_for
+    cap = capacity_for(rs)
+    mem = torch.empty(dbg.table_bytes(cap), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    g = dbg.Graph(31, cap, memory=mem, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g.insert(packed, offsets)
+    assert g.status() == dbg.OK
+    a = g.export()
+    g.close()
+    h = dbg.Graph(31, cap)
+    h.insert(packed, offsets)
+    assert_same(a, h.export())
+    h.close()
+    # misaligned or short memory is refused before any launch
+    with pytest.raises(dbg.DbgError):
+        dbg.Graph(31, cap, memory=mem[16:])
+    with pytest.raises(dbg.DbgError):
+        dbg.Graph(31, cap + 1, memory=mem)

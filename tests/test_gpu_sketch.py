@@ -50,3 +50,20 @@ def test_estimator_matches_the_formula_and_the_truth():
     assert est == pytest.approx(oracle.hll_estimate(regs), rel=1e-12)
     D = oracle.build_graph(rs.packed, rs.offsets, 31).n_vertices
     assert abs(est - D) <= 0.13 * D
+
+
+def test_batched_sketch_equals_one_by_one_and_oracle():
+    import torch
+    sets = [synth.ragged_reads(40 + 7 * i, 120, (21, 31, 5)[i % 3], 1300 + i, lead=i % 4)
+            for i in range(130)]  # two launches of up to 128 items; mixed k
+    sets[3] = synth.from_strings([], 21)  # an empty read set
+    dev = [to_device(rs) for rs in sets]
+    regs = torch.full((len(sets), dbg.SKETCH_REGISTERS + 1), 7, dtype=torch.int32, device="cuda")
+    dbg.sketch_batch([(rs.k, pk, of, regs[i]) for i, (rs, (pk, of)) in enumerate(zip(sets, dev))])
+    got = regs.cpu().numpy().view(np.uint32)
+    for i, (rs, (pk, of)) in enumerate(zip(sets, dev)):
+        assert got[i, -1] == dbg.OK
+        one = dbg.sketch(rs.k, pk, of).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got[i], one)
+        if i % 13 == 0:
+            assert np.array_equal(got[i, :-1], oracle.sketch(rs.packed, rs.offsets, rs.k))
