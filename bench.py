@@ -190,6 +190,19 @@ def time_oracle_sample(rs, seconds_target, threads, seed_reads=20_000):
 # our arm
 # ---------------------------------------------------------------------------
 
+def job_throughput(local_ms: float, units_per_rank: float, world: int, dist=None,
+                   device=None) -> tuple[float, float]:
+    """Whole-job throughput of `world` replicas: the units every rank
+    processed over the slowest rank's time (max over ranks).  Returns
+    (units per second, the max time in ms)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    return units_per_rank * world / (local_ms / 1e3), local_ms
+
+
 def run_ours(args):
     import torch
 
@@ -275,32 +288,36 @@ def run_ours(args):
     k2_ms = [a.elapsed_time(b) for a, b, c in ev]
     kt = g.kernel_times(K)
     g.enable_kernel_timing(0)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     st = g.status()
     if st != dbg.OK:
         raise RuntimeError(f"timed build failed: {dbg.STATUS_NAMES.get(st, st)}")
 
-    value = edges * K * world / (total_ms / 1e3)
+    value, total_ms = job_throughput(total_ms, edges * K, world, dist, dev)
     k1_mean_s = statistics.mean(k1_ms) / 1e3
     in_bytes = rs.packed.nbytes + rs.offsets.nbytes
-    # algorithmic bytes per launch of each kernel (see DESIGN.md, section 6)
-    kernel_bytes = {
-        "direct": touches * SECTOR_RMW_BYTES + in_bytes,
-        "bin_count": in_bytes,
-        "bin_scan": 0,
-        "bin_scatter": in_bytes + 8 * touches,
-        "bin_apply": 8 * touches + SECTOR_RMW_BYTES * D,
-        "direct_fallback": 0,
-    }
+    # algorithmic bytes per launch of each kernel
     names = dbg.Graph.KERNELS
     kernels = {}
     for j, name in enumerate(names):
         col = [float(x) for x in kt[:, j] if x >= 0]
         if col:
             kernels[name] = {"ms": statistics.mean(col), "launches_per_step": 1}
+    tiled = "bin_split" in kernels
+    if tiled:  # the split mark spans four kernels: units, count, offsets, scatter
+        kernels["bin_split"]["launches_per_step"] = 4
+    kernel_bytes = {
+        "direct": touches * SECTOR_RMW_BYTES + in_bytes,
+        "bin_count": in_bytes,
+        "bin_scan": 0,
+        "bin_scatter": in_bytes + 8 * touches,
+        # the second partition: every event read and written once
+        "bin_split": 16 * touches,
+        # tiled: events read once, every table slot read and written once;
+        # streaming: events read once, one sector read-modify-write per vertex
+        "bin_apply": 8 * touches + (2 * 32 * capacity if tiled else SECTOR_RMW_BYTES * D),
+        "bin_deferred": 0,
+        "direct_fallback": 0,
+    }
     launched = sum(1 for j in range(len(names)) if (kt[:, j] >= 0).any())
     dom = max(kernels, key=lambda n: kernels[n]["ms"])
     dom_s = kernels[dom]["ms"] / 1e3
@@ -361,6 +378,17 @@ def run_ours(args):
         e2e = {"value": edges * K * world / e2e_s, "unit": "edges/s",
                "h2d_bytes_per_step": int(rs.packed.nbytes + rs.offsets.nbytes),
                "d2h_bytes_per_step": 2 * 8 + 4}
+
+    # the sorted export (not part of a step), into device buffers
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    keys_d, counts_d = g.export_device(stream)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    export_ms = ea.elapsed_time(eb)
+    if keys_d.shape[0] != D:
+        raise RuntimeError("export size mismatch")
+    del keys_d, counts_d
     g.close()
 
     cpu = None
@@ -388,6 +416,7 @@ def run_ours(args):
             "insert_path": "binned" if "bin_apply" in kernels else "direct",
             "kernels": kernels,
             "k2_init_ms": statistics.mean(k2_ms),
+            "export_ms": export_ms,
             "step_ms_p50": float(np.percentile(step_ms, 50)),
             "step_ms_p99": float(np.percentile(step_ms, 99)),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -396,7 +425,7 @@ def run_ours(args):
                          "alg_bytes_per_launch": alg_bytes},
             "random_sector_probe": probe,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
-            "gpu_launches": (1 + launched) * K,
+            "gpu_launches": (1 + sum(v["launches_per_step"] for v in kernels.values())) * K,
             "kernel_source_digest": kernel_source_digest(),
         }
         print(json.dumps(line), flush=True)

@@ -28,7 +28,12 @@
  *     and adds nothing.
  *   - Vertex keys: the (k-1) bases of a vertex, 2 bits each, first base in
  *     the most significant position (so key order is lexicographic order
- *     with A < C < G < T).  2 <= k <= 32, so a key has at most 62 bits.
+ *     with A < C < G < T).  2 <= k <= 64.  For k <= 32 a key is one 64-bit
+ *     word (at most 62 bits); for k > 32 (the paper's default is k = 51,
+ *     Section "Code organization") it is a 128-bit integer of at most 126
+ *     bits, exported as two words per vertex, high word first.  Graphs with
+ *     k > 32 support create, insert (direct path), batch, stats, export and
+ *     normalize; spill, grow, the no-alloc export and contigs take k <= 32.
  *   - Counters: 32-bit unsigned, one per label in the order A, C, G, T,
  *     wrapping modulo 2^32 (the paper's are 8-bit, Section "Graph data
  *     structure"; the wider width keeps high-coverage repeats exact).
@@ -52,7 +57,8 @@ typedef enum dbg_status {
   DBG_ERR_BUFFER_TOO_SMALL = 5, /* export: max_n < number of vertices (n_out tells how many) */
   DBG_ERR_BAD_OFFSETS = 6,      /* sticky: the GPU saw offsets[r+1] < offsets[r] */
   DBG_ERR_NOALLOC_LIMIT = 7,    /* dbg_export_sorted_noalloc: graph larger than its fixed scratch */
-  DBG_ERR_NEEDS_GROW = 8        /* vertices were spilled (see dbg_set_spill): call dbg_grow */
+  DBG_ERR_NEEDS_GROW = 8,       /* vertices were spilled (see dbg_set_spill): call dbg_grow */
+  DBG_ERR_TIMEOUT = 9           /* a kernel gave up a bounded wait on a copy (sticky) */
 } dbg_status;
 
 typedef struct dbg_graph *dbg_handle;
@@ -70,7 +76,8 @@ typedef struct dbg_tuning {
   int apply_ctas;     /* binned apply: CTAs per SM (0: as many as fit) */
   int apply_counters; /* binned apply: work counters the warps draw chunks from, 1..64 (0: 16) */
   int region_log2;    /* binned: table region of 2^region_log2 slots, 16..26 (0: automatic) */
-  int apply_group;    /* binned apply: regions per launch (0: all regions in one launch) */
+  int apply_group;    /* binned apply (streaming): regions per launch (0: all in one launch) */
+  int apply_mode;     /* binned apply: 0 automatic (tiled), 1 streaming, 2 tiled */
 } dbg_tuning;
 
 typedef struct dbg_info {
@@ -83,7 +90,7 @@ typedef struct dbg_info {
   uint64_t spill_capacity; /* spill records (0: no spill buffer) */
 } dbg_info;
 
-/* Create an empty graph for k-mers of length k (2..32) with room for
+/* Create an empty graph for k-mers of length k (2..64) with room for
  * `capacity` vertices (>= 1).  The table is an open-addressing array of
  * `capacity` 32-byte slots (replacing the paper's array of N list heads,
  * Section "Graph data structure", Fig. 2), allocated on the current CUDA
@@ -138,10 +145,12 @@ int dbg_reserve_events(dbg_handle h, uint64_t events);
  * the last `calls` calls (0 turns it off).  Synchronizes the device. */
 int dbg_enable_kernel_timing(dbg_handle h, int calls);
 
-/* Kernel durations of the kept calls, oldest first: out_ms[6*c + j] for
+/* Kernel durations of the kept calls, oldest first: out_ms[8*c + j] for
  * kernel j = 0 direct insert, 1 bin count, 2 bin scan, 3 bin scatter, 4 bin
- * apply, 5 direct insert run as the binned fall-back (it returns at once when
- * the binned kernels did the work);
+ * split (the tiled apply's second partition pass, all its kernels), 5 bin
+ * apply, 6 bin deferred (the tiled apply's events that left their tile), 7
+ * direct insert run as the binned fall-back (it returns at once when the
+ * binned kernels did the work);
  * -1 for a kernel the call did not launch.  Waits for the recorded events.
  * *n_calls receives the number of calls written (at most max_calls). */
 int dbg_kernel_times(dbg_handle h, float *out_ms, int max_calls, int *n_calls);
@@ -238,14 +247,16 @@ int dbg_get_status(dbg_handle h, void *stream);
 int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *stream);
 
 /* Export the graph sorted by key (ascending, i.e. lexicographic with
- * A<C<G<T): keys_out[i] and counts_out[4*i .. 4*i+3] (labels A, C, G, T).
+ * A<C<G<T): keys_out[i] (for k > 32: keys_out[2*i] high word, keys_out[2*i+1]
+ * low word) and counts_out[4*i .. 4*i+3] (labels A, C, G, T).
  * Output pointers may be host or device memory (copied with
  * cudaMemcpyDefault); either may be NULL to skip it.  Waits for `stream`.
  * *n_out receives the number of vertices D.  If D > max_n nothing is
  * written and DBG_ERR_BUFFER_TOO_SMALL is returned (a call with max_n = 0
  * is therefore a size query).  Temporary device memory (about 48 bytes per
- * vertex) is taken from the stream-ordered allocator and released before
- * return.  Errors: INVALID_ARG, OOM, CUDA, BUFFER_TOO_SMALL, and the sticky
+ * vertex, 80 for k > 32) comes from a stream-ordered pool the library keeps
+ * per device (up to 1 GiB of it stays cached between calls) and is
+ * released to it before return.  Errors: INVALID_ARG, OOM, CUDA, BUFFER_TOO_SMALL, and the sticky
  * status (nothing exported when it is set). */
 int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, uint64_t max_n,
                       uint64_t *n_out, void *stream);

@@ -67,6 +67,8 @@ def _load():
     lib.oracle_shard_of_keys.restype = None
     lib.oracle_sketch.argtypes = [P, P, U64, I, P]
     lib.oracle_sketch.restype = I
+    lib.oracle_export_sorted_wide.argtypes = [P, P, P, U64]
+    lib.oracle_export_sorted_wide.restype = I
     lib.oracle_export_first.argtypes = [P, P, U64]
     lib.oracle_export_first.restype = I
     _lib = lib
@@ -76,7 +78,8 @@ def _load():
 @dataclass
 class Graph:
     """Sorted vertices: ``keys`` (uint64, A=0 C=1 G=2 T=3, first base most
-    significant) and ``counts`` (uint32 [D, 4], columns A, C, G, T)."""
+    significant; for k > 32 a [D, 2] array of the 128-bit key's high and low
+    words) and ``counts`` (uint32 [D, 4], columns A, C, G, T)."""
 
     k: int
     keys: np.ndarray
@@ -86,7 +89,7 @@ class Graph:
 
     @property
     def n_vertices(self) -> int:
-        return int(self.keys.size)
+        return int(self.keys.shape[0])
 
     def as_dict(self) -> dict:
         if self.strings is None:
@@ -109,9 +112,13 @@ def build_graph(packed: np.ndarray, offsets: np.ndarray, k: int, *, shard_mod: i
         raise RuntimeError(f"oracle_build failed with status {st}")
     try:
         n = int(lib.oracle_num_vertices(g))
-        keys = np.empty(n, dtype=np.uint64)
         counts = np.empty((n, 4), dtype=np.uint32)
-        st = lib.oracle_export_sorted(g, keys.ctypes.data, counts.ctypes.data, n)
+        if k > 32:
+            keys = np.empty((n, 2), dtype=np.uint64)
+            st = lib.oracle_export_sorted_wide(g, keys.ctypes.data, counts.ctypes.data, n)
+        else:
+            keys = np.empty(n, dtype=np.uint64)
+            st = lib.oracle_export_sorted(g, keys.ctypes.data, counts.ctypes.data, n)
         if st != 0:
             raise RuntimeError(f"oracle_export_sorted failed with status {st}")
         first = np.empty(n, dtype=np.uint8)
@@ -168,8 +175,11 @@ def hll_estimate(regs: np.ndarray) -> float:
     return raw
 
 
-def decode_key(key: int, k: int) -> str:
+def decode_key(key, k: int) -> str:
+    """The (k-1)-mer of a key (an int, or a (high, low) word pair for k > 32)."""
     m = k - 1
+    if not isinstance(key, int) and np.ndim(key) == 1:
+        key = (int(key[0]) << 64) | int(key[1])
     return "".join("ACGT"[(int(key) >> (2 * (m - 1 - j))) & 3] for j in range(m))
 
 

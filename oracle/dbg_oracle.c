@@ -255,7 +255,7 @@ void oracle_free(oracle_graph *g) {
  * bases.  2 <= k <= 32.  shard_mod >= 1, shard_id < shard_mod, n_threads >= 1. */
 int oracle_build(const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads, int k,
                  uint64_t shard_mod, uint64_t shard_id, int n_threads, oracle_graph **out) {
-  if (!out || k < 2 || k > 32 || shard_mod < 1 || shard_id >= shard_mod || n_threads < 1)
+  if (!out || k < 2 || k > 64 || shard_mod < 1 || shard_id >= shard_mod || n_threads < 1)
     return OR_ERR_ARG;
   if (!offsets) return OR_ERR_ARG;
   for (uint64_t r = 0; r < n_reads; ++r)
@@ -341,16 +341,44 @@ static int sorted_refs(const oracle_graph *g, ref_t **out, uint64_t *n_out) {
 }
 
 /* Vertices in lexicographic order (A<C<G<T): encoded keys and counters
- * [n][4] in A, C, G, T order.  Buffers hold at least max_n entries. */
+ * [n][4] in A, C, G, T order.  Buffers hold at least max_n entries.  Keys
+ * of k - 1 <= 32 bases only (oracle_export_sorted_wide takes any k). */
 int oracle_export_sorted(const oracle_graph *g, uint64_t *keys, uint32_t *counts, uint64_t max_n) {
+  ref_t *refs;
+  uint64_t n;
+  if (!g || (keys && g->k - 1 > 32)) return OR_ERR_ARG;
+  if (oracle_num_vertices(g) > max_n) return OR_ERR_ARG;
+  int st = sorted_refs(g, &refs, &n);
+  if (st != OR_OK) return st;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (keys) keys[i] = encode(refs[i].s, g->k - 1);
+    if (counts) memcpy(counts + 4 * i, refs[i].cnt, 4 * sizeof(uint32_t));
+  }
+  free(refs);
+  return OR_OK;
+}
+
+/* The same order with keys of up to 63 bases as 128-bit integers, the first
+ * base most significant: keys[2i] holds bits 64..127, keys[2i+1] bits 0..63. */
+int oracle_export_sorted_wide(const oracle_graph *g, uint64_t *keys, uint32_t *counts,
+                              uint64_t max_n) {
   ref_t *refs;
   uint64_t n;
   if (!g) return OR_ERR_ARG;
   if (oracle_num_vertices(g) > max_n) return OR_ERR_ARG;
   int st = sorted_refs(g, &refs, &n);
   if (st != OR_OK) return st;
+  const int m = g->k - 1;
   for (uint64_t i = 0; i < n; ++i) {
-    if (keys) keys[i] = encode(refs[i].s, g->k - 1);
+    uint64_t hi = 0, lo = 0;
+    for (int j = 0; j < m; ++j) { /* (hi, lo) = (hi, lo) * 4 + code */
+      hi = (hi << 2) | (lo >> 62);
+      lo = (lo << 2) | (uint64_t)label_column(refs[i].s[j]);
+    }
+    if (keys) {
+      keys[2 * i] = hi;
+      keys[2 * i + 1] = lo;
+    }
     if (counts) memcpy(counts + 4 * i, refs[i].cnt, 4 * sizeof(uint32_t));
   }
   free(refs);

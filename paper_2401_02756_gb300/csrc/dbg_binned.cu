@@ -30,6 +30,7 @@
 
 #include "dbg_binned.cuh"
 #include "dbg_tiles.cuh"
+#include "dbg_tma.cuh"
 
 namespace dbg {
 namespace {
@@ -247,7 +248,7 @@ constexpr size_t scatter_smem(int tile_reads, int parts) {
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, 4)
     k_bin_scatter(const __grid_constant__ ItemPack<1> pk, int tile_reads, int shift, int parts,
                   uint64_t slices, const uint32_t *hist, unsigned long long *cursor, uint64_t *out,
                   uint64_t cap, unsigned long long *ctr, const uint32_t *use_binned) {
@@ -428,6 +429,419 @@ __global__ void __launch_bounds__(BLOCK)
   }
 }
 
+// --- tiled apply -------------------------------------------------------------
+//
+// The streaming apply above keeps a table window in L2, but every event is
+// still a round trip to L2 (a load, then a CAS or an add): ncu shows it
+// stalled on those round trips, far below both the L2 and the DRAM peaks.
+// The tiled apply instead gives each table tile of kTileSlots slots (64 KB) to
+// one CTA: the CTA copies the tile into shared memory, applies every event
+// whose home slot lies in the tile with shared-memory CAS and add, and
+// writes the tile back.  The table then moves through DRAM once, in
+// coalesced 16-byte accesses, and no event leaves the SM.
+//
+// That needs the events grouped by tile.  The scatter pass grouped them by
+// region (2^shift slots = tiles_per_region tiles); a second, region-local
+// partition pass (split) orders each region's events by tile:
+//   units   -- each region's events are cut into units of `unit` events;
+//   count   -- per unit, a histogram over the region's tiles;
+//   offsets -- per region, the tiles' event ranges and each unit's place in
+//              every tile's range (a prefix over the units);
+//   scatter -- per unit, every event to its tile's range (second buffer).
+// A probe sequence that runs off the end of its tile (keys homed near the
+// end of a full stretch of slots) cannot continue there: the next tile
+// belongs to another CTA.  Such events are deferred to a list (in the first
+// event buffer, which the split pass has consumed) and applied afterwards,
+// from their home slot, with the direct insert's global find-or-claim; the
+// tile they would have spilled into is final by then.  A probe that reaches
+// max_probes inside its tile fails (or spills) exactly as in the direct
+// insert, so every key stays within max_probes of its home slot.
+
+constexpr int kTileLog2 = 11;
+constexpr int kTileSlots = 1 << kTileLog2;  // 2048 slots = 64 KB of shared memory
+constexpr int kMaxTilesPerRegion = 4096;    // beyond this the streaming apply is used
+
+constexpr int kBatch = 8;  // events each thread loads before it uses them (memory parallelism)
+
+struct TileAux {
+  uint32_t *unit_hist;            // [units][tpr] counts, then starts (relative to the region's)
+  unsigned long long *tile_begin; // [parts * tpr + 1]
+  unsigned long long *unit_base;  // [parts + 1]
+  unsigned long long *deferred;   // [1] events left for the global pass
+};
+
+// unit_base[p] = units of regions < p, each region cut into ceil(count/unit) units.
+__global__ void __launch_bounds__(1024)
+    k_tile_units(const unsigned long long *counts, int parts, uint64_t unit,
+                 unsigned long long *unit_base, unsigned long long *deferred,
+                 const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  __shared__ unsigned long long s_warp[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int p0 = 2 * tid;
+  const unsigned long long ua = p0 < parts ? (counts[p0] + unit - 1) / unit : 0ull;
+  const unsigned long long ub = p0 + 1 < parts ? (counts[p0 + 1] + unit - 1) / unit : 0ull;
+  const unsigned long long local = ua + ub;
+  unsigned long long incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = s_warp[lane];
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(kFull, w, d);
+      if (lane >= d) w += o;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  const unsigned long long b = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
+  if (p0 < parts) unit_base[p0] = b;
+  if (p0 + 1 < parts) unit_base[p0 + 1] = b + ua;
+  if (tid == 0) {
+    unit_base[parts] = s_warp[31];
+    *deferred = 0ull;
+  }
+}
+
+// Region of unit u (the last p with unit_base[p] <= u) and its event range.
+__device__ __forceinline__ int unit_region(const unsigned long long *unit_base, int parts,
+                                           uint64_t u) {
+  int lo = 0, hi = parts - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (unit_base[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t tile_in_region(uint64_t ev, uint64_t n_slots, int shift,
+                                                   int p) {
+  const uint64_t home = home_slot(ev >> 3, n_slots);
+  return (uint32_t)((home >> kTileLog2) - ((uint64_t)p << (shift - kTileLog2)));
+}
+
+// kBatch events of [base, b) strided by BLOCK, kEmpty past b (never an event:
+// events hold keys of at most 60 bits).
+template <int BLOCK>
+__device__ __forceinline__ void load_batch(const uint64_t *__restrict__ ev, uint64_t base,
+                                           uint64_t b, uint64_t (&e)[kBatch]) {
+#pragma unroll
+  for (int r = 0; r < kBatch; ++r) {
+    const uint64_t i = base + (uint64_t)r * BLOCK + threadIdx.x;
+    e[r] = i < b ? __ldcs(ev + i) : kEmpty;
+  }
+}
+
+// Per unit: histogram of its events over the region's tiles.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_tile_count(const uint64_t *__restrict__ ev, const unsigned long long *begin,
+                 TileAux aux, int parts, uint64_t unit, int shift, int tpr, uint64_t n_slots,
+                 const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  extern __shared__ uint32_t s_hist[];  // tpr
+  const uint64_t n_units = aux.unit_base[parts];
+  for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int p = unit_region(aux.unit_base, parts, u);
+    const uint64_t a = begin[p] + (u - aux.unit_base[p]) * unit;
+    const uint64_t b = min(a + unit, (uint64_t)begin[p + 1]);
+    for (int j = threadIdx.x; j < tpr; j += BLOCK) s_hist[j] = 0u;
+    __syncthreads();
+    for (uint64_t base = a; base < b; base += (uint64_t)BLOCK * kBatch) {
+      uint64_t e[kBatch];
+      load_batch<BLOCK>(ev, base, b, e);
+#pragma unroll
+      for (int r = 0; r < kBatch; ++r)
+        if (e[r] != kEmpty) atomicAdd(&s_hist[tile_in_region(e[r], n_slots, shift, p)], 1u);
+    }
+    __syncthreads();
+    uint32_t *h = aux.unit_hist + u * (uint64_t)tpr;
+    for (int j = threadIdx.x; j < tpr; j += BLOCK) h[j] = s_hist[j];
+    __syncthreads();
+  }
+}
+
+// Per region (one CTA each): every tile's event range (tile_begin, absolute)
+// and, in unit_hist, where each unit's events of each tile start (relative
+// to the region's first event).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_tile_offsets(const unsigned long long *begin, TileAux aux, int parts, int tpr,
+                   const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  __shared__ unsigned long long s_warp[BLOCK / 32];
+  const int p = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t u0 = aux.unit_base[p], u1 = aux.unit_base[p + 1];
+  unsigned long long *tb = aux.tile_begin + (uint64_t)p * tpr;
+  // each thread owns `per` consecutive tiles: their totals (kept in tb for now)
+  const int per = (tpr + BLOCK - 1) / BLOCK;
+  const int j0 = min(tpr, tid * per), j1 = min(tpr, j0 + per);
+  unsigned long long local = 0;
+  for (int j = j0; j < j1; ++j) {
+    unsigned long long total = 0;
+    for (uint64_t u = u0; u < u1; ++u) total += aux.unit_hist[u * (uint64_t)tpr + j];
+    tb[j] = total;
+    local += total;
+  }
+  unsigned long long incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < BLOCK / 32 ? s_warp[lane] : 0ull;
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(kFull, w, d);
+      if (lane >= d) w += o;
+    }
+    if (lane < BLOCK / 32) s_warp[lane] = w;
+  }
+  __syncthreads();
+  // tile j's range starts after the events of the region's tiles < j
+  unsigned long long rel = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
+  for (int j = j0; j < j1; ++j) {
+    const unsigned long long total = tb[j];
+    tb[j] = begin[p] + rel;
+    unsigned long long at = rel;
+    for (uint64_t u = u0; u < u1; ++u) {
+      uint32_t *c = aux.unit_hist + u * (uint64_t)tpr + j;
+      const uint32_t n = *c;
+      *c = (uint32_t)at;
+      at += n;
+    }
+    rel += total;
+  }
+  if (p == parts - 1 && tid == 0) aux.tile_begin[(uint64_t)parts * tpr] = begin[parts];
+}
+
+// Per unit: every event to its tile's range in the second buffer.  Each
+// chunk of BLOCK * kBatch events is counting-sorted by tile in shared memory
+// first, so that every tile's run of the chunk is written by consecutive
+// threads to consecutive addresses (coalesced stores instead of one scattered
+// 8-byte store per event).
+template <int BLOCK>
+constexpr size_t tile_scatter_smem(int tpr) {
+  return (size_t)BLOCK * kBatch * (8 + 4) + (size_t)tpr * 12;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_tile_scatter(const uint64_t *__restrict__ ev, uint64_t *__restrict__ ev2,
+                   const unsigned long long *begin, TileAux aux, int parts, uint64_t unit,
+                   int shift, int tpr, uint64_t n_slots, const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  constexpr int C = BLOCK * kBatch;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *s_ev = reinterpret_cast<uint64_t *>(smem);       // C, in tile order
+  uint32_t *s_tile = reinterpret_cast<uint32_t *>(s_ev + C);  // C: tile of s_ev[i]
+  uint32_t *s_at = s_tile + C;                                // tpr: next start (unit cursor)
+  uint32_t *s_hist = s_at + tpr;                              // tpr: chunk counts
+  uint32_t *s_off = s_hist + tpr;                             // tpr: chunk prefix
+  __shared__ uint32_t s_warp[BLOCK / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (tpr + BLOCK - 1) / BLOCK;  // bins per thread in the prefix
+  const int j0 = min(tpr, tid * per), j1 = min(tpr, j0 + per);
+  const uint64_t n_units = aux.unit_base[parts];
+  for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int p = unit_region(aux.unit_base, parts, u);
+    const uint64_t a = begin[p] + (u - aux.unit_base[p]) * unit;
+    const uint64_t b = min(a + unit, (uint64_t)begin[p + 1]);
+    const uint32_t *h = aux.unit_hist + u * (uint64_t)tpr;
+    for (int j = tid; j < tpr; j += BLOCK) s_at[j] = h[j];
+    uint64_t *out = ev2 + begin[p];
+    for (uint64_t base = a; base < b; base += C) {
+      for (int j = tid; j < tpr; j += BLOCK) s_hist[j] = 0u;
+      __syncthreads();
+      uint64_t e[kBatch];
+      uint32_t where[kBatch];  // tile << 16 | rank (rank < C <= 65536)
+      load_batch<BLOCK>(ev, base, b, e);
+#pragma unroll
+      for (int r = 0; r < kBatch; ++r) {
+        if (e[r] != kEmpty) {
+          const uint32_t t = tile_in_region(e[r], n_slots, shift, p);
+          where[r] = (t << 16) | atomicAdd(&s_hist[t], 1u);
+        }
+      }
+      __syncthreads();
+      // exclusive prefix of the chunk's tile counts
+      uint32_t local = 0;
+      for (int j = j0; j < j1; ++j) local += s_hist[j];
+      uint32_t incl = local;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += o;
+      }
+      if (lane == 31) s_warp[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t w = lane < BLOCK / 32 ? s_warp[lane] : 0u;
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t o = __shfl_up_sync(kFull, w, d);
+          if (lane >= d) w += o;
+        }
+        if (lane < BLOCK / 32) s_warp[lane] = w;
+      }
+      __syncthreads();
+      uint32_t run = incl - local + (warp > 0 ? s_warp[warp - 1] : 0u);
+      for (int j = j0; j < j1; ++j) {
+        s_off[j] = run;
+        run += s_hist[j];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kBatch; ++r) {
+        if (e[r] != kEmpty) {
+          const uint32_t t = where[r] >> 16;
+          const uint32_t i = s_off[t] + (where[r] & 0xFFFFu);
+          s_ev[i] = e[r];
+          s_tile[i] = t;
+        }
+      }
+      __syncthreads();
+      const uint32_t n = (uint32_t)min((uint64_t)C, b - base);
+      for (uint32_t i = tid; i < n; i += BLOCK) {
+        const uint32_t t = s_tile[i];
+        out[s_at[t] + (i - s_off[t])] = s_ev[i];
+      }
+      __syncthreads();
+      for (int j = tid; j < tpr; j += BLOCK) s_at[j] += s_hist[j];
+      __syncthreads();
+    }
+  }
+}
+
+// One event against the tile in shared memory: found or claimed and counted,
+// failed (max_probes inside the tile), or deferred (the probe left the tile).
+__device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint64_t first, int len,
+                                           uint64_t n_slots, uint32_t max_probes,
+                                           uint32_t *status, SpillRecord *spill,
+                                           uint64_t spill_cap, unsigned long long *spill_count,
+                                           uint64_t *deferred_ev, unsigned long long *deferred) {
+  const unsigned long long key = e >> 3;
+  int q = (int)(home_slot(key, n_slots) - first);
+  uint32_t probes = 0;
+  while (q < len) {
+    const unsigned long long cur = st[q].key;
+    bool found = cur == key;
+    if (!found && cur == kEmpty) {
+      const unsigned long long prev = atomicCAS(&st[q].key, kEmpty, key);
+      found = prev == kEmpty || prev == key;
+    }
+    if (found) {
+      if (e & 4ull) atomicAdd(&st[q].cnt[e & 3ull], 1u);
+      return;
+    }
+    if (++probes >= max_probes) {
+      spill_or_fail(spill, spill_cap, spill_count, status, key, (e & 4ull) != 0,
+                    (uint32_t)(e & 3ull));
+      return;
+    }
+    ++q;
+  }
+  deferred_ev[atomicAdd(deferred, 1ull)] = e;  // left the tile: later, globally
+}
+
+// Persistent CTAs take tiles: a bulk copy brings the tile into shared memory
+// while the threads load their first events; the events are applied there;
+// a bulk copy writes the tile back while the CTA moves to its next tile.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_tile_apply(const uint64_t *__restrict__ ev2, uint64_t *deferred_ev, TileAux aux,
+                 uint64_t n_tiles, Slot *table, uint64_t n_slots, uint32_t max_probes,
+                 uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
+                 unsigned long long *spill_count, const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  Slot *st = reinterpret_cast<Slot *>(smem);  // kTileSlots slots
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint32_t s_stop, s_failed;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+    s_failed = 0u;
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint64_t a = aux.tile_begin[t], b = aux.tile_begin[t + 1];
+    const uint64_t first = t << kTileLog2;
+    // no event, or a tile past the table's end (never has one): the tile stays
+    // as it is (the same decision for the whole CTA)
+    if (a == b || first >= n_slots) continue;
+    const int len = (int)min((uint64_t)kTileSlots, n_slots - first);
+    const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(Slot);
+    if (threadIdx.x == 0) {
+      s_stop = ld_volatile_u32(status);
+      bulk_wait_read_all();  // the previous tile's write-back has left `st`
+      mbar_expect_tx(&s_bar, bytes);
+      bulk_load(st, table + first, bytes, &s_bar);
+    }
+    uint64_t e[kBatch];
+    load_batch<BLOCK>(ev2, a, b, e);  // overlaps the tile's arrival
+    if (!mbar_wait(&s_bar, parity)) atomicExch(&s_failed, 1u);
+    parity ^= 1u;
+    __syncthreads();
+    if (s_failed) {
+      if (threadIdx.x == 0) {
+        set_sticky(status, DBG_ERR_TIMEOUT);
+        mbar_wait(&s_bar, parity ^ 1u);  // give the copy one more bounded chance to land
+        bulk_wait_all();
+      }
+      return;
+    }
+    if (s_stop == 0u) {  // an earlier error stops the insert, as in the direct kernel
+      for (uint64_t base = a;;) {
+#pragma unroll
+        for (int r = 0; r < kBatch; ++r)
+          if (e[r] != kEmpty)
+            tile_event(e[r], st, first, len, n_slots, max_probes, status, spill, spill_cap,
+                       spill_count, deferred_ev, aux.deferred);
+        base += (uint64_t)BLOCK * kBatch;
+        if (base >= b) break;
+        load_batch<BLOCK>(ev2, base, b, e);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_stop == 0u) {
+      fence_proxy_async_smem();  // the CTA's shared-memory updates, before the bulk read
+      bulk_store(table + first, st, bytes);
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
+}
+
+// The deferred events, from their home slots, with the global find-or-claim.
+__global__ void k_tile_deferred(const uint64_t *__restrict__ deferred_ev, TileAux aux,
+                                Slot *table, uint64_t n_slots, uint32_t max_probes,
+                                uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
+                                unsigned long long *spill_count, const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  const uint64_t n = *aux.deferred;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t e = deferred_ev[i];
+    const unsigned long long key = e >> 3;
+    uint64_t s;
+    if (find_or_claim(table, n_slots, max_probes, key, s)) {
+      if (e & 4ull) atomicAdd(&table[s].cnt[e & 3ull], 1u);
+    } else {
+      spill_or_fail(spill, spill_cap, spill_count, status, key, (e & 4ull) != 0,
+                    (uint32_t)(e & 3ull));
+    }
+  }
+}
+
 int ceil_log2(uint64_t x) {
   int r = 0;
   while ((1ull << r) < x) ++r;
@@ -482,7 +896,8 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events) {
   if (h->bin_cap != events) {
     DBG_CK(cudaDeviceSynchronize());  // earlier binned calls may still read the old buffer
     cudaFree(h->bin_ev);
-    h->bin_ev = nullptr;
+    cudaFree(h->bin_ev2);  // the tiled apply's buffer follows the event capacity
+    h->bin_ev = h->bin_ev2 = nullptr;
     h->bin_cap = 0;
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, events * sizeof(uint64_t));
@@ -493,6 +908,71 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events) {
   return DBG_OK;
 }
 
+
+namespace {
+
+uint64_t tile_unit(int tpr) { return std::max<uint64_t>(16384, 64ull * (uint64_t)tpr); }
+
+// Layout of the tiled apply's aux buffer for a geometry.
+struct TileAuxLayout {
+  size_t hist, tile_begin, unit_base, deferred, total;
+};
+
+TileAuxLayout tile_aux_layout(uint64_t bin_cap, const BinGeometry &geo, int tpr) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const uint64_t max_units = bin_cap / tile_unit(tpr) + (uint64_t)geo.parts;
+  TileAuxLayout l;
+  l.hist = 0;
+  l.tile_begin = al(l.hist + max_units * (uint64_t)tpr * 4);
+  l.unit_base = al(l.tile_begin + ((uint64_t)geo.parts * tpr + 1) * 8);
+  l.deferred = al(l.unit_base + ((uint64_t)geo.parts + 1) * 8);
+  l.total = al(l.deferred + 8);
+  return l;
+}
+
+TileAux tile_aux(dbg_handle h, const BinGeometry &geo, int tpr) {
+  const TileAuxLayout l = tile_aux_layout(h->bin_cap, geo, tpr);
+  char *b = static_cast<char *>(h->bin_aux);
+  TileAux a;
+  a.unit_hist = reinterpret_cast<uint32_t *>(b + l.hist);
+  a.tile_begin = reinterpret_cast<unsigned long long *>(b + l.tile_begin);
+  a.unit_base = reinterpret_cast<unsigned long long *>(b + l.unit_base);
+  a.deferred = reinterpret_cast<unsigned long long *>(b + l.deferred);
+  return a;
+}
+
+// The second event buffer and the aux buffer of the tiled apply; false (and
+// the streaming apply is used) if they cannot be had -- out of memory, or
+// inside a stream capture that began before they existed.
+bool ensure_tile_scratch(dbg_handle h, const BinGeometry &geo, int tpr, bool capturing) {
+  const size_t need = tile_aux_layout(h->bin_cap, geo, tpr).total;
+  if (h->bin_ev2 && h->bin_aux && h->bin_aux_bytes >= need) return true;
+  if (capturing) return false;
+  if (cudaDeviceSynchronize() != cudaSuccess) return false;  // earlier calls may use them
+  if (!h->bin_ev2) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, h->bin_cap * sizeof(uint64_t)) != cudaSuccess) {
+      cudaGetLastError();  // clear the allocation failure
+      return false;
+    }
+    h->bin_ev2 = static_cast<uint64_t *>(p);
+  }
+  if (h->bin_aux_bytes < need) {
+    cudaFree(h->bin_aux);
+    h->bin_aux = nullptr;
+    h->bin_aux_bytes = 0;
+    void *p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    h->bin_aux = p;
+    h->bin_aux_bytes = need;
+  }
+  return true;
+}
+
+}  // namespace
 
 template <int B, int U, int M>
 int launch_apply(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int sms,
@@ -525,6 +1005,21 @@ int launch_apply_m(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int
     case 16: return launch_apply<B, U, 16>(h, mv, geo, sms, t, s);
     default: return launch_apply<B, U, 8>(h, mv, geo, sms, t, s);
   }
+}
+
+template <int BT>
+int launch_tile_scatter(dbg_handle h, const MetaView &mv, const TileAux &aux,
+                        const BinGeometry &geo, uint64_t unit, int tpr, int sms, cudaStream_t s) {
+  const size_t smem = tile_scatter_smem<BT>(tpr);
+  // (set even below 48 KB: the kernel's static shared memory counts too)
+  DBG_CK(cudaFuncSetAttribute(k_tile_scatter<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+  int per_sm = 0;
+  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_scatter<BT>, BT, smem));
+  k_tile_scatter<BT><<<std::max(1, per_sm) * sms, BT, smem, s>>>(
+      h->bin_ev, h->bin_ev2, mv.begin, aux, geo.parts, unit, geo.shift, tpr, h->n_slots, mv.flag);
+  DBG_CK(cudaGetLastError());
+  return DBG_OK;
 }
 
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
@@ -578,17 +1073,72 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
                                            mv.cursor, h->bin_ev, h->bin_cap, mv.ctr, mv.flag);
     DBG_CK(cudaGetLastError());
   }
-  timer_mark(h, call, 4, s);
-  switch (t.apply_unroll) {
-    case 2: DBG_TRY(launch_apply_m<B, 2>(h, mv, geo, sms, t, s)); break;
-    case 8: DBG_TRY(launch_apply_m<B, 8>(h, mv, geo, sms, t, s)); break;
-    default: DBG_TRY(launch_apply_m<B, 4>(h, mv, geo, sms, t, s)); break;
+  const int tpr = 1 << std::max(0, geo.shift - kTileLog2);
+  // (unit starts are kept in 32 bits relative to their region: the event
+  // buffer must stay below 2^32 events)
+  const bool tiled = t.apply_mode != 1 && geo.shift >= kTileLog2 &&
+                     tpr <= kMaxTilesPerRegion && h->bin_cap < (1ull << 32) &&
+                     ensure_tile_scratch(h, geo, tpr, capturing);
+  if (tiled) {
+    const uint64_t unit = tile_unit(tpr);
+    const TileAux aux = tile_aux(h, geo, tpr);
+    const uint64_t n_tiles = (uint64_t)geo.parts * tpr;
+    timer_mark(h, call, 4, s);
+    k_tile_units<<<1, 1024, 0, s>>>(mv.counts, geo.parts, unit, aux.unit_base, aux.deferred,
+                                    mv.flag);
+    DBG_CK(cudaGetLastError());
+    {
+      int per_sm = 0;
+      DBG_CK(cudaFuncSetAttribute(k_tile_count<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tpr * 4));
+      DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_count<B>, B,
+                                                           (size_t)tpr * 4));
+      k_tile_count<B><<<std::max(1, per_sm) * sms, B, (size_t)tpr * 4, s>>>(
+          h->bin_ev, mv.begin, aux, geo.parts, unit, geo.shift, tpr, h->n_slots, mv.flag);
+      DBG_CK(cudaGetLastError());
+    }
+    k_tile_offsets<B><<<geo.parts, B, 0, s>>>(mv.begin, aux, geo.parts, tpr, mv.flag);
+    DBG_CK(cudaGetLastError());
+    // chunks of 8 events per thread: larger blocks for more tiles per region,
+    // so that each tile's run in a chunk stays several events long
+    if (tpr <= 256) {
+      DBG_TRY(launch_tile_scatter<256>(h, mv, aux, geo, unit, tpr, sms, s));
+    } else if (tpr <= 512) {
+      DBG_TRY(launch_tile_scatter<512>(h, mv, aux, geo, unit, tpr, sms, s));
+    } else {
+      DBG_TRY(launch_tile_scatter<1024>(h, mv, aux, geo, unit, tpr, sms, s));
+    }
+    timer_mark(h, call, 5, s);
+    {
+      constexpr size_t smem = (size_t)kTileSlots * sizeof(Slot);
+      DBG_CK(cudaFuncSetAttribute(k_tile_apply<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+      int per_sm = 0;
+      DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_apply<B>, B, smem));
+      const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)std::max(1, per_sm) * sms);
+      k_tile_apply<B><<<(int)grid, B, smem, s>>>(
+          h->bin_ev2, h->bin_ev, aux, n_tiles, h->table, h->n_slots, h->max_probes, h->d_status,
+          h->d_spill, h->spill_cap, h->d_spill_count, mv.flag);
+      DBG_CK(cudaGetLastError());
+    }
+    timer_mark(h, call, 6, s);
+    k_tile_deferred<<<sms * 4, 256, 0, s>>>(h->bin_ev, aux, h->table, h->n_slots, h->max_probes,
+                                            h->d_status, h->d_spill, h->spill_cap,
+                                            h->d_spill_count, mv.flag);
+    DBG_CK(cudaGetLastError());
+  } else {
+    timer_mark(h, call, 5, s);
+    switch (t.apply_unroll) {
+      case 2: DBG_TRY(launch_apply_m<B, 2>(h, mv, geo, sms, t, s)); break;
+      case 8: DBG_TRY(launch_apply_m<B, 8>(h, mv, geo, sms, t, s)); break;
+      default: DBG_TRY(launch_apply_m<B, 4>(h, mv, geo, sms, t, s)); break;
+    }
   }
   // the direct insert runs only if the events did not fit the buffer
-  timer_mark(h, call, 5, s);
+  timer_mark(h, call, 7, s);
   const int st = launch_insert(&it, 1, tiles, tuning, h->sm_count, s, mv.flag);
   if (st != DBG_OK) return st;
-  timer_mark(h, call, 6, s);
+  timer_mark(h, call, 8, s);
   if (!capturing) DBG_CK(cudaEventRecord(h->bin_done, s));
   return DBG_OK;
 }

@@ -69,16 +69,18 @@ __device__ __forceinline__ int out_degree(const Slot &sl, uint32_t &label) {
   return d;
 }
 
-__global__ void k_normalize(Slot *t, uint64_t n, double divisor) {
+// (cnt0: the first counter's 32-bit word in the slot -- 2, or 4 for k > 32)
+__global__ void k_normalize(Slot *t, uint64_t n, double divisor, int cnt0) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     if (t[i].key == kEmpty) continue;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(t + i) + cnt0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const uint32_t c = t[i].cnt[b];
+      const uint32_t c = cnt[b];
       if (!c) continue;
       const double q = floor((double)c / divisor + 0.5);
-      t[i].cnt[b] = q >= 4294967295.0 ? 0xffffffffu : (uint32_t)q;
+      cnt[b] = q >= 4294967295.0 ? 0xffffffffu : (uint32_t)q;
     }
   }
 }
@@ -267,7 +269,8 @@ extern "C" int dbg_normalize(dbg_handle h, double divisor, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int st = dbg_get_status(h, stream);  // complete graphs only
   if (st != DBG_OK) return st;
-  k_normalize<<<std::max(1, h->sm_count) * 8, 256, 0, s>>>(h->table, h->n_slots, divisor);
+  k_normalize<<<std::max(1, h->sm_count) * 8, 256, 0, s>>>(h->table, h->n_slots, divisor,
+                                                             h->k > 32 ? 4 : 2);
   DBG_CK(cudaGetLastError());
   return DBG_OK;
 }
@@ -276,7 +279,7 @@ extern "C" int dbg_find_contigs(dbg_handle h, char *bases_out, uint64_t max_base
                                 uint64_t *offsets_out, uint64_t max_contigs, uint64_t *n_contigs,
                                 uint64_t *n_bases, void *stream) {
   using namespace dbg;
-  if (!h || !n_contigs || !n_bases) return DBG_ERR_INVALID_ARG;
+  if (!h || !n_contigs || !n_bases || h->k > 32) return DBG_ERR_INVALID_ARG;
   Guard g(h->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

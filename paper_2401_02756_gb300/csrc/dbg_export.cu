@@ -83,6 +83,7 @@ extern "C" int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *cou
   *n_out = D;
   if (D > max_n) return DBG_ERR_BUFFER_TOO_SMALL;
   if (D == 0) return DBG_OK;
+  if (h->k > 32) return export_sorted_wide(h, D, keys_out, counts_out, s);
 
   const int end_bit = 2 * (h->k - 1);
   size_t temp_bytes = 0;

@@ -102,7 +102,7 @@ __global__ void k_gather_noalloc(const Slot *t, const unsigned long long *idx, u
 extern "C" int dbg_export_sorted_noalloc(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out,
                                          uint64_t max_n, uint64_t *n_out, void *stream) {
   using namespace dbg;
-  if (!h || !n_out || !keys_out || !counts_out) return DBG_ERR_INVALID_ARG;
+  if (!h || !n_out || !keys_out || !counts_out || h->k > 32) return DBG_ERR_INVALID_ARG;
   int prev = 0;
   DBG_CK(cudaGetDevice(&prev));
   if (prev != h->device) DBG_CK(cudaSetDevice(h->device));

@@ -202,6 +202,9 @@ struct dbg_graph {
   // binned insert scratch (allocated when a binned insert first needs it)
   uint64_t *bin_ev = nullptr;               // events, 8 bytes each
   uint64_t bin_cap = 0;                     // capacity in events
+  uint64_t *bin_ev2 = nullptr;              // tiled apply: events again, grouped by table tile
+  void *bin_aux = nullptr;                  // tiled apply: unit histograms, tile ranges, counters
+  uint64_t bin_aux_bytes = 0;
   unsigned long long *bin_meta = nullptr;   // region counts, ranges, cursors, flag
   cudaEvent_t bin_done = nullptr;           // orders binned calls that share the scratch
   // optional per-kernel timing of insert calls (dbg_enable_kernel_timing)
@@ -215,9 +218,9 @@ namespace dbg {
 
 // Kernel boundaries of one insert call for the optional timer: mark i is
 // recorded before kernel i; the last mark after the last kernel.
-//   0 direct insert | 1 bin count | 2 bin scan | 3 bin scatter | 4 bin apply |
-//   5 gated direct insert (binned fall-back) | 6 end
-constexpr int kTimerMarks = 7;
+//   0 direct insert | 1 bin count | 2 bin scan | 3 bin scatter | 4 bin split |
+//   5 bin apply | 6 bin deferred | 7 gated direct insert (binned fall-back) | 8 end
+constexpr int kTimerMarks = 9;
 constexpr int kTimerKernels = kTimerMarks - 1;
 
 // Start recording a call (no-op when timing is off); returns the ring slot.
@@ -274,6 +277,11 @@ dbg_tuning resolve_tuning(const dbg_tuning &t);
 
 // Table kernels.
 int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream);
-int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, cudaStream_t stream);
+int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, cudaStream_t stream,
+                 bool wide);
+// Graphs with k > 32 (128-bit keys, dbg_wide.cu).
+int launch_insert_wide(const ItemDesc &it, int sm_count, cudaStream_t s);
+int export_sorted_wide(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts_out,
+                       cudaStream_t s);
 
 }  // namespace dbg

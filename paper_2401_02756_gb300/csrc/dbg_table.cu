@@ -82,7 +82,8 @@ __global__ void k_table_init(uint4 *t, uint64_t n_vec) {
 }
 
 // Vertices (occupied slots) and edges (sum of counters) of a table.
-__global__ void k_stats(const Slot *t, uint64_t n_slots, unsigned long long *acc) {
+// (wide: keys of k > 32 take two words, so the counters sit at byte 16)
+__global__ void k_stats(const Slot *t, uint64_t n_slots, unsigned long long *acc, int wide) {
   unsigned long long nv = 0, ne = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += stride) {
@@ -91,7 +92,8 @@ __global__ void k_stats(const Slot *t, uint64_t n_slots, unsigned long long *acc
     const unsigned long long key = (unsigned long long)a.x | ((unsigned long long)a.y << 32);
     if (key != kEmpty) {
       nv += 1;
-      ne += (unsigned long long)a.z + a.w + b.x + b.y;
+      ne += wide ? (unsigned long long)b.x + b.y + b.z + b.w
+                 : (unsigned long long)a.z + a.w + b.x + b.y;
     }
   }
   for (int d = 16; d > 0; d >>= 1) {
@@ -120,14 +122,15 @@ int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream) {
   return DBG_OK;
 }
 
-int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, cudaStream_t stream) {
+int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, cudaStream_t stream,
+                 bool wide) {
   int dev = 0, sms = 0;
   DBG_CK(cudaGetDevice(&dev));
   DBG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   DBG_CK(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), stream));
   const uint64_t want = (n_slots + 255) / 256;
   const int grid = (int)std::min<uint64_t>(want, (uint64_t)stream_grid(sms, 8));
-  k_stats<<<std::max(grid, 1), 256, 0, stream>>>(table, n_slots, acc);
+  k_stats<<<std::max(grid, 1), 256, 0, stream>>>(table, n_slots, acc, wide ? 1 : 0);
   DBG_CK(cudaGetLastError());
   return DBG_OK;
 }
@@ -205,7 +208,7 @@ int ensure_copy_stream(dbg_handle h) {
 int check_create_args(int k, uint64_t capacity, dbg_handle *out) {
   if (!out) return DBG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (k < 2 || k > 32 || capacity == 0 || capacity > (~0ull / sizeof(dbg::Slot)) - 256)
+  if (k < 2 || k > 64 || capacity == 0 || capacity > (~0ull / sizeof(dbg::Slot)) - 256)
     return DBG_ERR_INVALID_ARG;
   return DBG_OK;
 }
@@ -309,7 +312,8 @@ extern "C" void dbg_destroy(dbg_handle h) {
   // cudaFree waits for the device anyway; a handle on caller memory that
   // allocated nothing itself frees only host state and does not wait
   const bool owns_device_memory = h->owns_slots || h->owns_small || h->stage_packed[0] ||
-                                  h->stage_offsets[0] || h->bin_ev || h->bin_meta || h->d_spill;
+                                  h->stage_offsets[0] || h->bin_ev || h->bin_meta || h->d_spill ||
+                                  h->bin_ev2 || h->bin_aux;
   if (owns_device_memory) cudaDeviceSynchronize();
   if (h->owns_slots) cudaFree(h->table);
   if (h->owns_small) cudaFree(h->d_status);
@@ -321,6 +325,8 @@ extern "C" void dbg_destroy(dbg_handle h) {
   }
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   cudaFree(h->bin_ev);
+  cudaFree(h->bin_ev2);
+  cudaFree(h->bin_aux);
   cudaFree(h->bin_meta);
   cudaFree(h->d_spill);
   if (h->bin_done) cudaEventDestroy(h->bin_done);
@@ -363,6 +369,7 @@ extern "C" int dbg_set_tuning(dbg_handle h, const dbg_tuning *t) {
   if (r.apply_counters < 0 || r.apply_counters > 64) return DBG_ERR_INVALID_ARG;
   if (r.region_log2 != 0 && (r.region_log2 < 16 || r.region_log2 > 26)) return DBG_ERR_INVALID_ARG;
   if (r.apply_group < 0) return DBG_ERR_INVALID_ARG;
+  if (r.apply_mode < 0 || r.apply_mode > 2) return DBG_ERR_INVALID_ARG;
   h->tuning = r;
   return DBG_OK;
 }
@@ -380,7 +387,7 @@ extern "C" int dbg_get_info(dbg_handle h, dbg_info *out) {
 }
 
 extern "C" int dbg_set_spill(dbg_handle h, uint64_t records) {
-  if (!h) return DBG_ERR_INVALID_ARG;
+  if (!h || (h->k > 32 && records > 0)) return DBG_ERR_INVALID_ARG;  // 64-bit spill records
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   DBG_CK(cudaDeviceSynchronize());
@@ -400,7 +407,7 @@ extern "C" int dbg_set_spill(dbg_handle h, uint64_t records) {
 }
 
 extern "C" int dbg_grow(dbg_handle h, uint64_t new_capacity, void *stream) {
-  if (!h) return DBG_ERR_INVALID_ARG;
+  if (!h || h->k > 32) return DBG_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   return dbg::launch_grow(h, new_capacity, static_cast<cudaStream_t>(stream));
@@ -480,6 +487,12 @@ bool want_binned(dbg_handle h) {
 
 int insert_one(dbg_handle h, const dbg::ItemDesc &it, uint64_t tiles, cudaStream_t s) {
   const int call = dbg::timer_begin_call(h);
+  if (h->k > 32) {  // 128-bit keys: their own kernel
+    dbg::timer_mark(h, call, 0, s);
+    const int st = dbg::launch_insert_wide(it, h->sm_count, s);
+    dbg::timer_mark(h, call, 1, s);
+    return st;
+  }
   if (want_binned(h) && (h->bin_cap > 0 || dbg::ensure_bin_scratch(h, 0) == DBG_OK))
     return dbg::launch_binned(h, it, tiles, h->tuning, s, call);
   dbg::timer_mark(h, call, 0, s);
@@ -645,7 +658,7 @@ extern "C" int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *
     if (items[i].n_reads == 0) continue;
     dbg_handle h = items[i].graph;
     dbg::ItemDesc it = dbg::make_item(h, items[i].packed, items[i].offsets, items[i].n_reads, 0);
-    if (want_binned(h)) {
+    if (want_binned(h) || h->k > 32) {  // their own kernels, one item at a time
       const dbg_tuning th = dbg::resolve_tuning(h->tuning);
       const int st = insert_one(h, it, (items[i].n_reads + th.tile_reads - 1) / th.tile_reads, s);
       if (st != DBG_OK) return st;
@@ -681,7 +694,7 @@ extern "C" int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, 
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int st = dbg::launch_stats(h->table, h->n_slots, h->d_acc, s);
+  int st = dbg::launch_stats(h->table, h->n_slots, h->d_acc, s, h->k > 32);
   if (st != DBG_OK) return st;
   unsigned long long acc[2] = {0, 0};
   uint32_t status = 0;
@@ -733,6 +746,7 @@ extern "C" const char *dbg_strerror(int code) {
     case DBG_ERR_BAD_OFFSETS: return "offsets are not non-decreasing";
     case DBG_ERR_NOALLOC_LIMIT: return "graph larger than the no-alloc export's fixed scratch";
     case DBG_ERR_NEEDS_GROW: return "vertices were spilled: call dbg_grow to complete the graph";
+    case DBG_ERR_TIMEOUT: return "a kernel gave up a bounded wait on an asynchronous copy";
     default: return "unknown status";
   }
 }

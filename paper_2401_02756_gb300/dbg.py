@@ -19,10 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdbg.so")
 
 (OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_BUFFER_TOO_SMALL, ERR_BAD_OFFSETS,
- ERR_NOALLOC_LIMIT, ERR_NEEDS_GROW) = range(9)
+ ERR_NOALLOC_LIMIT, ERR_NEEDS_GROW, ERR_TIMEOUT) = range(10)
 STATUS_NAMES = {0: "DBG_OK", 1: "DBG_ERR_INVALID_ARG", 2: "DBG_ERR_OOM", 3: "DBG_ERR_CAPACITY",
                 4: "DBG_ERR_CUDA", 5: "DBG_ERR_BUFFER_TOO_SMALL", 6: "DBG_ERR_BAD_OFFSETS",
-                7: "DBG_ERR_NOALLOC_LIMIT", 8: "DBG_ERR_NEEDS_GROW"}
+                7: "DBG_ERR_NOALLOC_LIMIT", 8: "DBG_ERR_NEEDS_GROW", 9: "DBG_ERR_TIMEOUT"}
 NOALLOC_EXPORT_MAX_VERTICES = 1 << 19
 
 EXPORTED = [
@@ -55,7 +55,7 @@ class Tuning(ctypes.Structure):
                 ("insert_path", ctypes.c_int), ("apply_unroll", ctypes.c_int),
                 ("apply_chunk", ctypes.c_int), ("apply_ctas", ctypes.c_int),
                 ("apply_counters", ctypes.c_int), ("region_log2", ctypes.c_int),
-                ("apply_group", ctypes.c_int)]
+                ("apply_group", ctypes.c_int), ("apply_mode", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -241,7 +241,7 @@ class Graph:
 
     TUNING_FIELDS = ("block_threads", "tile_reads", "grid_ctas", "warp_aggregate", "insert_path",
                      "apply_unroll", "apply_chunk", "apply_ctas", "apply_counters", "region_log2",
-                     "apply_group")
+                     "apply_group", "apply_mode")
 
     def set_tuning(self, **fields) -> None:
         """Launch shape and path of the insert; fields (all optional, 0 = automatic):
@@ -260,19 +260,21 @@ class Graph:
         t = Tuning(*[int(vals[f]) for f in self.TUNING_FIELDS])
         _check(load().dbg_set_tuning(self.handle, ctypes.byref(t)), "dbg_set_tuning")
 
-    KERNELS = ("direct", "bin_count", "bin_scan", "bin_scatter", "bin_apply", "direct_fallback")
+    KERNELS = ("direct", "bin_count", "bin_scan", "bin_scatter", "bin_split", "bin_apply",
+               "bin_deferred", "direct_fallback")
 
     def enable_kernel_timing(self, calls: int) -> None:
         """Record CUDA events around each kernel of the next insert calls (keep ``calls``)."""
         _check(load().dbg_enable_kernel_timing(self.handle, int(calls)), "dbg_enable_kernel_timing")
 
     def kernel_times(self, max_calls: int = 1024) -> np.ndarray:
-        """[calls, 6] kernel durations in ms (-1: not launched), oldest call first."""
-        buf = (ctypes.c_float * (6 * max_calls))()
+        """[calls, len(KERNELS)] kernel durations in ms (-1: not launched), oldest first."""
+        K = len(self.KERNELS)
+        buf = (ctypes.c_float * (K * max_calls))()
         n = ctypes.c_int()
         _check(load().dbg_kernel_times(self.handle, buf, max_calls, ctypes.byref(n)),
                "dbg_kernel_times")
-        return np.frombuffer(buf, dtype=np.float32)[: 6 * n.value].reshape(n.value, 6).copy()
+        return np.frombuffer(buf, dtype=np.float32)[: K * n.value].reshape(n.value, K).copy()
 
     def set_spill(self, records: int) -> None:
         """Keep vertices that find no slot in a spill buffer of ``records``
@@ -319,11 +321,13 @@ class Graph:
         return int(nv.value), int(ne.value)
 
     def export(self, stream=None, out=None) -> tuple[np.ndarray, np.ndarray]:
-        """Sorted vertices: keys (uint64 [D]) and counters (uint32 [D, 4], A C G T).
-        ``out`` = (keys, counts) host arrays (pinned for speed) of at least D
-        rows makes it one call into them; the views [:D] are returned."""
+        """Sorted vertices: keys (uint64 [D], or [D, 2] high and low words for
+        k > 32) and counters (uint32 [D, 4], A C G T).  ``out`` = (keys,
+        counts) host arrays (pinned for speed) of at least D rows makes it one
+        call into them; the views [:D] are returned."""
         L = load()
         n = ctypes.c_uint64()
+        wide = self.k > 32
         if out is not None:
             keys, counts = out
             st = L.dbg_export_sorted(self.handle, keys.ctypes.data, counts.ctypes.data,
@@ -337,7 +341,7 @@ class Graph:
         if st not in (OK, ERR_BUFFER_TOO_SMALL):
             raise DbgError(st, "dbg_export_sorted")
         D = int(n.value)
-        keys = np.empty(D, dtype=np.uint64)
+        keys = np.empty((D, 2) if wide else D, dtype=np.uint64)
         counts = np.empty((D, 4), dtype=np.uint32)
         if D:
             _check(L.dbg_export_sorted(self.handle, keys.ctypes.data, counts.ctypes.data, D,
@@ -368,7 +372,8 @@ class Graph:
         return [raw[int(offs[i]):int(offs[i + 1])] for i in range(n.value)]
 
     def export_device(self, stream=None):
-        """Sorted vertices as CUDA tensors (int64 keys [D], int32 counters [D, 4])."""
+        """Sorted vertices as CUDA tensors (int64 keys [D], or [D, 2] for k > 32;
+        int32 counters [D, 4])."""
         import torch
         L = load()
         n = ctypes.c_uint64()
@@ -376,7 +381,7 @@ class Graph:
         if st not in (OK, ERR_BUFFER_TOO_SMALL):
             raise DbgError(st, "dbg_export_sorted")
         D = int(n.value)
-        keys = torch.empty(D, dtype=torch.int64, device="cuda")
+        keys = torch.empty((D, 2) if self.k > 32 else D, dtype=torch.int64, device="cuda")
         counts = torch.empty((D, 4), dtype=torch.int32, device="cuda")
         if D:
             _check(L.dbg_export_sorted(self.handle, keys.data_ptr(), counts.data_ptr(), D,

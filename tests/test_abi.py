@@ -67,7 +67,7 @@ def test_pack_ascii_phase_and_rejection(lib):
 def test_argument_errors_return_before_any_launch(lib):
     h = ctypes.c_void_p()
     assert lib.dbg_create(1, 10, ctypes.byref(h)) == dbg.ERR_INVALID_ARG
-    assert lib.dbg_create(33, 10, ctypes.byref(h)) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_create(65, 10, ctypes.byref(h)) == dbg.ERR_INVALID_ARG
     assert lib.dbg_create(21, 0, ctypes.byref(h)) == dbg.ERR_INVALID_ARG
     assert lib.dbg_create(21, 10, None) == dbg.ERR_INVALID_ARG
     assert lib.dbg_insert_reads(None, None, None, 5, None) == dbg.ERR_INVALID_ARG

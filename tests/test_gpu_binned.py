@@ -122,26 +122,35 @@ def test_auto_path_picks_binned_for_large_tables():
 def test_kernel_timer_records_the_kernels_each_path_launches():
     rs = synth.ragged_reads(1500, 200, 21, 39)
     packed, offsets = to_device(rs)
-    for path, launched in ((1, [0]), (2, [1, 2, 3, 4, 5])):
+    K = len(dbg.Graph.KERNELS)
+    for tuning, launched in ((dict(insert_path=1), [0]),
+                             (dict(insert_path=2), [1, 2, 3, 4, 5, 6, 7]),
+                             (dict(insert_path=2, apply_mode=1), [1, 2, 3, 5, 7])):
         g = dbg.Graph(rs.k, MULTI_REGION)
-        g.set_tuning(insert_path=path)
+        g.set_tuning(**tuning)
         g.enable_kernel_timing(4)
         for _ in range(6):  # more calls than kept: the oldest are dropped
             g.insert(packed, offsets)
         t = g.kernel_times()
-        assert t.shape == (4, 6)
-        for j in range(6):
+        assert t.shape == (4, K)
+        for j in range(K):
             if j in launched:
-                assert (t[:, j] >= 0).all(), (path, j, t)
+                assert (t[:, j] >= 0).all(), (tuning, j, t)
             else:
-                assert (t[:, j] == -1).all(), (path, j, t)
+                assert (t[:, j] == -1).all(), (tuning, j, t)
         g.close()
 
 
 @pytest.mark.parametrize("tuning", [
-    dict(apply_unroll=2), dict(apply_unroll=8), dict(apply_chunk=4), dict(apply_chunk=16),
-    dict(apply_ctas=1), dict(apply_counters=1), dict(apply_counters=64),
-    dict(region_log2=16), dict(region_log2=26, apply_chunk=4, apply_unroll=2),
+    # the streaming apply and its launch shapes
+    dict(apply_mode=1), dict(apply_mode=1, apply_unroll=2), dict(apply_mode=1, apply_unroll=8),
+    dict(apply_mode=1, apply_chunk=4), dict(apply_mode=1, apply_chunk=16),
+    dict(apply_mode=1, apply_ctas=1), dict(apply_mode=1, apply_counters=1),
+    dict(apply_mode=1, apply_counters=64), dict(apply_mode=1, region_log2=16),
+    dict(apply_mode=1, region_log2=26, apply_chunk=4, apply_unroll=2),
+    # the tiled apply over region sizes of 32 .. 4096 tiles (2^26: streaming fall-back)
+    dict(apply_mode=2), dict(apply_mode=2, region_log2=16), dict(apply_mode=2, region_log2=20),
+    dict(apply_mode=2, region_log2=23), dict(apply_mode=2, region_log2=26),
 ])
 def test_binned_tuning_independence(tuning):
     rs = synth.ragged_reads(2500, 250, 27, 40, lead=1)
@@ -150,4 +159,37 @@ def test_binned_tuning_independence(tuning):
     g.insert(packed, offsets)
     assert g.status() == dbg.OK
     assert_same_graph(g.export(), oracle_export(rs))
+    g.close()
+
+
+@pytest.mark.parametrize("fill", [1.1, 1.3, 1.5])
+def test_tiled_apply_at_high_load_defers_exactly(fill):
+    # a nearly full table: long probe runs, many of them past a tile's end
+    rs = synth.ragged_reads(6000, 300, 25, 41, lead=2)
+    exp = oracle_export(rs)
+    cap = int(len(exp[0]) * fill) + 1
+    for mode in (1, 2):
+        g = dbg.Graph(rs.k, cap)
+        g.set_tuning(insert_path=2, apply_mode=mode)
+        packed, offsets = to_device(rs)
+        g.insert(packed, offsets)
+        assert g.status() == dbg.OK
+        assert_same_graph(g.export(), exp)
+        g.close()
+
+
+def test_tiled_apply_respects_max_probes_with_a_spill():
+    rs = synth.ragged_reads(4000, 250, 21, 42)
+    exp = oracle_export(rs)
+    g = dbg.Graph(rs.k, int(len(exp[0]) * 1.05) + 1, max_probes=16)
+    g.set_tuning(insert_path=2, apply_mode=2)
+    g.set_spill(2_000_000)
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    st = g.status()
+    assert st in (dbg.OK, dbg.ERR_NEEDS_GROW)
+    if st == dbg.ERR_NEEDS_GROW:
+        g.grow(4 * g.info()["n_slots"])
+    assert g.status() == dbg.OK
+    assert_same_graph(g.export(), exp)
     g.close()

@@ -246,7 +246,7 @@ def test_shards_and_threads_partition_the_graph():
 
 def test_invalid_arguments_rejected():
     rs = synth.from_strings(["ACGT"], 3)
-    for k in (1, 33):
+    for k in (1, 65):  # keys of up to 63 bases (k <= 64)
         with pytest.raises(RuntimeError):
             oracle.build_graph(rs.packed, rs.offsets, k)
     with pytest.raises(RuntimeError):
@@ -491,3 +491,39 @@ def test_normalization_removes_errors_and_keeps_the_genome():
     got = oc.find_contigs(g.keys, norm, k)
     # the genome minus its thinly covered ends, in one piece
     assert len(got) == 1 and got[0] in genome and len(got[0]) > len(genome) - 150
+
+
+# --------------------------------------------------------------------------
+# k > 32 (the paper's default k = 51): 128-bit keys
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [33, 40, 51, 64])
+def test_wide_k_matches_brute_force(k):
+    rs = synth.ragged_reads(40, 2 * k, k, 600 + k, lead=k % 4)
+    reads = [rs.read_ascii(r) for r in range(rs.n_reads)]
+    g = oracle.build_graph(rs.packed, rs.offsets, k, strings=True)
+    assert g.as_dict() == brute_force(reads, k)
+
+
+@pytest.mark.parametrize("k", [33, 51, 64])
+def test_wide_keys_encode_the_strings_in_order(k):
+    rs = synth.ragged_reads(60, 150, k, 700 + k)
+    g = oracle.build_graph(rs.packed, rs.offsets, k, strings=True)
+    assert g.keys.shape == (g.n_vertices, 2)
+    assert [oracle.decode_key(x, k) for x in g.keys] == g.strings
+    as_int = [(int(h) << 64) | int(lo) for h, lo in g.keys]
+    assert all(a < b for a, b in zip(as_int[:-1], as_int[1:]))
+    assert max(as_int) < (1 << (2 * (k - 1)))  # 126 bits at most: the high word is never all ones
+    # the same vertices as a narrow build would have, by string (no truncation)
+    ln = rs.lengths()
+    assert int(g.counts.astype(np.int64).sum()) == int(np.maximum(ln - k + 1, 0).sum())
+
+
+def test_paper_default_k51_single_read():
+    # one random 400-base read (no repeated 50-mer): a path of 351 vertices
+    read = synth.codes_to_ascii(synth.random_genome(400, 51))
+    rs = synth.from_strings([read], 51)
+    g = oracle.build_graph(rs.packed, rs.offsets, 51, strings=True)
+    assert sorted(read[j:j + 50] for j in range(351)) == g.strings
+    out = {s: int(c.sum()) for s, c in zip(g.strings, g.counts)}
+    assert out[read[-50:]] == 0 and sum(out.values()) == 350
