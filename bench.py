@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: device memory budget")
+    ap.add_argument("--downstream", action="store_true",
+                    help="also time normalization and contigs on the built table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
@@ -85,7 +87,8 @@ def measured_peaks():
 
 def kernel_source_digest():
     h = hashlib.sha256()
-    for f in ("dbg_insert.cu", "dbg_binned.cu", "dbg_binned.cuh", "dbg_tiles.cuh", "dbg_internal.cuh"):
+    for f in ("dbg_insert.cu", "dbg_binned.cu", "dbg_binned.cuh", "dbg_tiles.cuh", "dbg_internal.cuh",
+              "dbg_tma.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2401_02756_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -389,6 +392,31 @@ def run_ours(args):
     if keys_d.shape[0] != D:
         raise RuntimeError("export size mismatch")
     del keys_d, counts_d
+
+    # the paper's downstream passes on the resident table: normalization
+    # (divisor = edges / genome size) and contigs (Alg. 5), each timed once
+    downstream = None
+    if args.downstream:
+        import ctypes
+        L = dbg.load()
+        div = edges / float(rs.meta.get("genome_len") or 1)
+        ea.record(stream)
+        g.normalize(div, stream)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        norm_ms = ea.elapsed_time(eb)
+        nc, nb = ctypes.c_uint64(), ctypes.c_uint64()
+        t_c = time.perf_counter()
+        st_c = L.dbg_find_contigs(g.handle, None, 0, None, 0, ctypes.byref(nc), ctypes.byref(nb),
+                                  stream.cuda_stream)
+        contig_s = time.perf_counter() - t_c
+        if st_c not in (dbg.OK, dbg.ERR_BUFFER_TOO_SMALL):
+            raise RuntimeError(f"contigs failed: {dbg.STATUS_NAMES.get(st_c, st_c)}")
+        downstream = {"divisor": div, "normalize_ms": norm_ms,
+                      "contigs_ms_size_pass": contig_s * 1e3, "contigs": int(nc.value),
+                      "contig_bases": int(nb.value),
+                      "note": "contig time is the first (sizing) call: marks, starts, sort, "
+                              "walk lengths, scan; the second call repeats it and writes"}
     g.close()
 
     cpu = None
@@ -417,6 +445,7 @@ def run_ours(args):
             "kernels": kernels,
             "k2_init_ms": statistics.mean(k2_ms),
             "export_ms": export_ms,
+            "downstream": downstream,
             "step_ms_p50": float(np.percentile(step_ms, 50)),
             "step_ms_p99": float(np.percentile(step_ms, 99)),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -524,6 +553,12 @@ def run_batch(args):
             size_ms.append(a.elapsed_time(b))
     preds = pred.predict_registers(regs, len(samples))
     graphs = [dbg.Graph(rs.k, pred.capacity(p)) for rs, p in zip(samples, preds)]
+    for rs, g in zip(samples, graphs):
+        # tables large enough for the binned path get an event buffer for all
+        # their vertex positions (high-coverage samples exceed the default of
+        # four per slot and would fall back to the direct insert)
+        if g.info()["table_bytes"] >= (256 << 20):
+            g.reserve_events(int(np.maximum(rs.lengths() - rs.k + 2, 0).sum()))
     items = [(g, pk, of) for g, (pk, of) in zip(graphs, dev_in)]
 
     def reset_all():

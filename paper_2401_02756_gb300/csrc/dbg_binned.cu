@@ -1,31 +1,31 @@
 // The binned insert: the same table updates as the direct insert kernel
 // (find or claim the prefix and suffix vertices, count the label -- Alg. 2-4
-// and the addRightVertex prose), issued in an order that keeps the table
-// region being updated resident in L2.
+// and the addRightVertex prose), issued in an order that keeps them on chip.
 //
 // A random 32-byte slot of a table far larger than L2 costs a DRAM round trip
-// that fetches a whole 128-byte line, which caps the direct insert near the
-// random-sector rate of HBM.  The same load + atomicAdd pattern on an
-// L2-resident region runs about 9x faster.  So for a large table and a large
-// call, the insert runs in four kernels:
-//   K1b count   -- walk the read tiles, compute every vertex's key and home
-//                  slot, and histogram the vertices by table region
-//                  (region = 2^shift consecutive slots, at most 2048 regions);
-//   K1c scan    -- exclusive prefix of the histogram: each region's event range;
-//   K1d scatter -- walk the tiles again and write one 8-byte event per vertex,
-//                  (key << 3) | (edge << 2) | label, into its region's range
-//                  (block-local counting sort in shared memory, one global
-//                  atomicAdd per non-empty region per 2048 events, coalesced
-//                  stores);
-//   K1e apply   -- stream the events in region order and apply them to the
-//                  table with the insert's own find-or-claim and atomicAdd:
-//                  all CTAs sweep the regions together, so the table lines
-//                  they touch are L2 hits after their first miss.
+// that fetches a whole line, which caps the direct insert near the
+// random-sector rate of HBM.  So for a large table the insert runs as:
+//   count   -- walk the read tiles, compute every vertex's key and home slot,
+//              and histogram the vertices by table region (2^shift slots,
+//              at most 2048 regions) per slice of tiles;
+//   scan    -- exclusive prefix of the histogram: each region's event range;
+//   scatter -- walk the tiles again and write one 8-byte event per vertex,
+//              (key << 3) | (edge << 2) | label, into its region's range
+//              (block-local counting sort in shared memory, run writes);
+//   split   -- per region, order the events by 2048-slot table tile
+//              (units of events: histogram, offsets, counting-sorted scatter);
+//   apply   -- one CTA per tile: a bulk copy brings the tile into shared
+//              memory, the tile's events are applied there with
+//              shared-memory CAS and add, a bulk copy writes it back;
+//   deferred -- the few events whose probe left their tile, from their home
+//              slot, with the global find-or-claim.
+// The earlier streaming apply (all CTAs sweep the region-ordered events with
+// global atomics inside an L2-resident window) remains as apply_mode = 1.
 // The result is identical to the direct insert (additions commute).  Events
-// hold a key of at most 60 bits, so the binned path serves k <= 31.  K1c
-// checks that the events fit the handle's event buffer; if not, K1d/K1e do
-// nothing and the direct insert kernel, launched after them with the same
-// flag as its gate, does the work instead.
+// hold a key of at most 60 bits, so the binned path serves k <= 31.  The scan
+// checks that the events fit the handle's event buffer; if not, every later
+// binned kernel returns at once and the direct insert kernel, launched last
+// with the same flag as its gate, does the work instead.
 #include <algorithm>
 
 #include "dbg_binned.cuh"
@@ -37,7 +37,6 @@ namespace {
 
 constexpr int kMaxParts = kBinMaxParts;
 constexpr int kRun = 8;             // consecutive vertex positions per thread (rolled keys)
-constexpr int kRoundEvents = 2048;  // events buffered per scatter flush (256 threads x kRun)
 
 __device__ __forceinline__ uint64_t make_event(uint64_t key, bool edge, uint32_t label) {
   return (key << 3) | ((uint64_t)edge << 2) | (uint64_t)label;
@@ -157,8 +156,8 @@ __global__ void __launch_bounds__(1024)
 template <int BLOCK>
 struct ScatterVisitor {
   static constexpr bool kUniformRounds = true;
-  static_assert(BLOCK * kRun == kRoundEvents, "one round is one flush");
-  uint64_t *sorted;    // kRoundEvents, in region order
+  static constexpr int kRound = BLOCK * kRun;  // events of one round = one flush
+  uint64_t *sorted;    // kRound, in region order
   uint16_t *spid;      // region of sorted[j]
   uint32_t *hist;      // parts: events per region in this round
   uint32_t *off;       // parts: exclusive prefix of hist
@@ -243,12 +242,12 @@ struct ScatterVisitor {
 
 template <int BLOCK>
 constexpr size_t scatter_smem(int tile_reads, int parts) {
-  return tile_smem_bytes(tile_reads) + (size_t)kRoundEvents * (8 + 2) +
+  return tile_smem_bytes(tile_reads) + (size_t)BLOCK * kRun * (8 + 2) +
          (size_t)parts * (4 + 4 + 8 + 8) + 64;
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 4)
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
     k_bin_scatter(const __grid_constant__ ItemPack<1> pk, int tile_reads, int shift, int parts,
                   uint64_t slices, const uint32_t *hist, unsigned long long *cursor, uint64_t *out,
                   uint64_t cap, unsigned long long *ctr, const uint32_t *use_binned) {
@@ -257,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK, 4)
   unsigned char *p = smem + tile_smem_bytes(tile_reads);
   ScatterVisitor<BLOCK> vis;
   vis.sorted = reinterpret_cast<uint64_t *>(p);
-  p += kRoundEvents * 8;
+  p += (size_t)ScatterVisitor<BLOCK>::kRound * 8;
   vis.gbase = reinterpret_cast<unsigned long long *>(p);
   p += (size_t)parts * 8;
   vis.cur = reinterpret_cast<unsigned long long *>(p);
@@ -1070,13 +1069,17 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   DBG_CK(cudaGetLastError());
   timer_mark(h, call, 3, s);
   {
-    const size_t smem = scatter_smem<B>(tile_reads, geo.parts);
-    DBG_CK(cudaFuncSetAttribute(k_bin_scatter<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // 512 threads: flushes of 4096 events, so that a region's run in a flush
+    // is long enough to fill whole sectors (shorter runs cost the L2 a
+    // read-modify-write of partly written sectors)
+    constexpr int BS = 512;
+    const size_t smem = scatter_smem<BS>(tile_reads, geo.parts);
+    DBG_CK(cudaFuncSetAttribute(k_bin_scatter<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<B>, B, smem));
+    DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<BS>, BS, smem));
     const int grid = (int)std::min<uint64_t>(slices, (uint64_t)std::max(1, per_sm) * sms);
-    k_bin_scatter<B><<<grid, B, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices, mv.hist,
-                                           mv.cursor, h->bin_ev, h->bin_cap, mv.ctr, mv.flag);
+    k_bin_scatter<BS><<<grid, BS, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices, mv.hist,
+                                             mv.cursor, h->bin_ev, h->bin_cap, mv.ctr, mv.flag);
     DBG_CK(cudaGetLastError());
   }
   const int tpr = 1 << std::max(0, geo.shift - kTileLog2);
