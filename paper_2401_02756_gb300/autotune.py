@@ -5,9 +5,9 @@ it); only the speed does.  :func:`tune` times candidate settings on the
 caller's own read set and table -- each trial empties the table, inserts the
 reads, and is timed with CUDA events on the insert's stream -- and leaves the
 fastest setting on the graph.  Candidates cover the insert path (direct or
-binned), the direct kernel's block size, tile size and warp aggregation, and
-the binned apply pass's probe slots per thread, chunk length, CTAs per SM and
-table region size.
+binned), the direct kernel's block size, tile size and warp aggregation, the
+binned path's region size and apply mode (tiled or streaming), and the
+streaming apply's probe slots per thread, chunk length and CTAs per SM.
 """
 
 from __future__ import annotations
@@ -23,7 +23,11 @@ def candidates(k: int, binned: bool) -> list[dict]:
     out = [dict(insert_path=1, block_threads=b, tile_reads=tr, warp_aggregate=a)
            for b, tr, a in itertools.product((128, 256), (64, 0), (0, 1))]
     if binned and k <= 31:
-        out += [dict(insert_path=2, apply_unroll=u, apply_chunk=m, apply_ctas=c, region_log2=r)
+        # the tiled apply over region sizes (0: its default of 2^20 slots)
+        out += [dict(insert_path=2, apply_mode=2, region_log2=r) for r in (0, 19, 21)]
+        # the streaming apply's launch shapes
+        out += [dict(insert_path=2, apply_mode=1, apply_unroll=u, apply_chunk=m, apply_ctas=c,
+                     region_log2=r)
                 for u, m, c, r in itertools.product((2, 4), (4, 8, 16), (0, 3), (0, 20))]
     return out
 

@@ -36,4 +36,5 @@ def test_tune_picks_a_candidate_and_keeps_the_graph_exact():
 def test_default_candidates_cover_both_paths():
     c = autotune.candidates(31, binned=True)
     assert {x["insert_path"] for x in c} == {1, 2}
+    assert {x.get("apply_mode") for x in c if x["insert_path"] == 2} == {1, 2}
     assert all(x["insert_path"] == 1 for x in autotune.candidates(32, binned=True))
