@@ -600,6 +600,29 @@ def run_batch(args):
             if g.status() != dbg.OK:
                 raise RuntimeError(f"{name}: build failed")
     D = np.array([g.stats()[0] for g in graphs], dtype=np.float64)
+
+    # without a predictor, plain per-sample launches need the sizes another
+    # way: a pilot build of each sample in a table of all its vertex
+    # positions (one table per k, emptied between samples; the emptying is
+    # not timed), then the vertex count
+    touches = [int(np.maximum(rs.lengths() - rs.k + 2, 0).sum()) for rs in samples]
+    pilots = {}
+    for rs, t in zip(samples, touches):
+        pilots[rs.k] = max(pilots.get(rs.k, 0), t)
+    pilots = {k: dbg.Graph(k, n + 64) for k, n in pilots.items()}
+    pilot_ms = 0.0
+    for rs, (pk, of) in zip(samples, dev_in):
+        p = pilots[rs.k]
+        p.reset(stream)
+        a, b = ev(), ev()
+        a.record(stream)
+        p.insert(pk, of, stream=stream)
+        p.stats(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pilot_ms += a.elapsed_time(b)
+    for p in pilots.values():
+        p.close()
     mlp = np.array([p.mlp for p in preds])
     hll = np.array([p.hll for p in preds])
     for g in graphs:
@@ -629,6 +652,9 @@ def run_batch(args):
         "batched_over_per_sample": pm / bm,
         "sizing_ms": sm,
         "batched_predicted_edges_per_s": edges / ((gm + sm) / 1e3),
+        "pilot_sizing_ms": pilot_ms,
+        "per_sample_with_pilot_sizing_edges_per_s": edges / ((pm + pilot_ms) / 1e3),
+        "batched_predicted_over_per_sample_with_pilot_sizing": (pm + pilot_ms) / (gm + sm),
         "batch_ms_p50": float(np.percentile(results["batched_graph"], 50)),
         "batch_ms_p99": float(np.percentile(results["batched_graph"], 99)),
         "predictor_error": {"network": err(mlp), "hyperloglog": err(hll),
