@@ -193,6 +193,25 @@ def time_oracle_sample(rs, seconds_target, threads, seed_reads=20_000):
 # our arm
 # ---------------------------------------------------------------------------
 
+def path_roofline(edges, touches, in_bytes, insert_s, peak_gbs, probe):
+    """The whole insert against the two ceilings of a hash-table build: HBM
+    (every vertex touch a 32-byte sector read and written, plus the input)
+    and the measured random-sector atomic rate on a table-sized buffer.  The
+    roofline is the lower of the two; the binned insert can pass the atomic
+    one because it does not touch the table at random."""
+    edge_bytes = (touches * SECTOR_RMW_BYTES + in_bytes) / edges
+    hbm = peak_gbs * 1e9 / edge_bytes
+    achieved = edges / insert_s
+    out = {"unit": "edges/s", "achieved": achieved, "bytes_per_edge": edge_bytes,
+           "hbm_ceiling": hbm, "frac_of_hbm_ceiling": achieved / hbm,
+           "atomic_ceiling": None, "frac_of_atomic_ceiling": None}
+    if probe:
+        atomic = probe["load_red_touches_per_s"] * edges / touches
+        out.update(atomic_ceiling=atomic, frac_of_atomic_ceiling=achieved / atomic,
+                   roofline=min(hbm, atomic), frac_of_roofline=achieved / min(hbm, atomic))
+    return out
+
+
 def job_throughput(local_ms: float, units_per_rank: float, world: int, dist=None,
                    device=None) -> tuple[float, float]:
     """Whole-job throughput of `world` replicas: the units every rank
@@ -310,7 +329,8 @@ def run_ours(args):
         kernels["bin_split"]["launches_per_step"] = 4
     kernel_bytes = {
         "direct": touches * SECTOR_RMW_BYTES + in_bytes,
-        "bin_count": in_bytes,
+        # tiled: the read offsets only (bucket sizing); streaming: the count pass reads the input
+        "bin_count": (rs.offsets.nbytes if tiled else in_bytes),
         "bin_scan": 0,
         "bin_scatter": in_bytes + 8 * touches,
         # the second partition: every event read and written once
@@ -453,6 +473,7 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
                          "alg_bytes_per_launch": alg_bytes},
             "random_sector_probe": probe,
+            "path_roofline": path_roofline(edges, touches, in_bytes, k1_mean_s, peak, probe),
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
             "gpu_launches": (1 + sum(v["launches_per_step"] for v in kernels.values())) * K,
             "kernel_source_digest": kernel_source_digest(),

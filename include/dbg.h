@@ -135,9 +135,15 @@ int dbg_reset(dbg_handle h, void *stream);
  * Errors: INVALID_ARG for out-of-range fields. */
 int dbg_set_tuning(dbg_handle h, const dbg_tuning *t);
 
-/* Size the binned insert's event buffer for `events` vertex positions per call
- * (8 bytes each; 0 = the default of 4 per table slot), allocating it now.
- * Synchronizes the device if the buffer grows.  Errors: INVALID_ARG, OOM. */
+/* Size the binned insert's event buffers for `events` vertex positions per
+ * call, plus a margin for the per-region buckets (events / 16 + 589,824;
+ * 0 = the default of 4.25 per table slot), allocating the first (8 bytes per
+ * event) now; the tiled apply adds a second one of the same size on its
+ * first call.  Read sets with more positions per slot than the buffer allows
+ * (high coverage into a tight table) should reserve their position count,
+ * sum over reads of max(0, length - k + 2); otherwise those calls take the
+ * direct insert.  Synchronizes the device if the buffer grows.  Errors:
+ * INVALID_ARG, OOM. */
 int dbg_reserve_events(dbg_handle h, uint64_t events);
 
 /* Measurement aid: record CUDA events around every kernel of the next insert
@@ -146,7 +152,8 @@ int dbg_reserve_events(dbg_handle h, uint64_t events);
 int dbg_enable_kernel_timing(dbg_handle h, int calls);
 
 /* Kernel durations of the kept calls, oldest first: out_ms[8*c + j] for
- * kernel j = 0 direct insert, 1 bin count, 2 bin scan, 3 bin scatter, 4 bin
+ * kernel j = 0 direct insert, 1 bin count (with the tiled apply: the bucket
+ * sizing that replaces the count), 2 bin scan, 3 bin scatter, 4 bin
  * split (the tiled apply's second partition pass, all its kernels), 5 bin
  * apply, 6 bin deferred (the tiled apply's events that left their tile), 7
  * direct insert run as the binned fall-back (it returns at once when the
@@ -169,13 +176,17 @@ int dbg_get_info(dbg_handle h, dbg_info *out);
  *
  * Two paths give the same graph.  The direct path is one kernel that updates
  * the table as it walks the reads.  The binned path (k <= 31) first writes
- * one 8-byte event per vertex position grouped by table region, then applies
- * the events region by region so the table lines being updated stay in L2;
- * it is chosen automatically for tables of 256 MiB or more and needs an event
- * buffer owned by the handle (default 4 events per slot, allocated by the
- * first call that needs it, or sized with dbg_reserve_events).  A call with
- * more vertex positions than the buffer holds runs the direct kernel instead
- * (decided on the device).  Binned calls on one handle run one after another.
+ * one 8-byte event per vertex position grouped by table region, then groups
+ * each region's events by 2048-slot tile and applies every tile in shared
+ * memory (one CTA per tile, the tile moved by bulk copies), so the table
+ * crosses DRAM once in whole lines; events whose probe leaves their tile are
+ * applied afterwards from their home slots.  It is chosen automatically for
+ * tables of 256 MiB or more and needs event buffers owned by the handle
+ * (default 4.25 events per slot, 16 bytes per event across its two buffers,
+ * allocated by the first call that needs them, or sized with
+ * dbg_reserve_events).  A call with more vertex positions than the buffer
+ * holds runs the direct kernel instead (decided on the device).  Binned calls
+ * on one handle run one after another.
  * Errors: INVALID_ARG (NULL handle, NULL pointer with n_reads > 0), OOM (event
  * buffer), CUDA; sticky CAPACITY / BAD_OFFSETS. */
 int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,

@@ -5,13 +5,14 @@
 // A random 32-byte slot of a table far larger than L2 costs a DRAM round trip
 // that fetches a whole line, which caps the direct insert near the
 // random-sector rate of HBM.  So for a large table the insert runs as:
-//   count   -- walk the read tiles, compute every vertex's key and home slot,
-//              and histogram the vertices by table region (2^shift slots,
-//              at most 2048 regions) per slice of tiles;
-//   scan    -- exclusive prefix of the histogram: each region's event range;
-//   scatter -- walk the tiles again and write one 8-byte event per vertex,
-//              (key << 3) | (edge << 2) | label, into its region's range
-//              (block-local counting sort in shared memory, run writes);
+//   buckets -- the read set's vertex positions, and for every table region
+//              (2^shift slots, at most 2048 regions) a bucket of its
+//              expected events plus six standard deviations;
+//   scatter -- walk the read tiles, compute every vertex's key and home
+//              slot, and write one 8-byte event per vertex,
+//              (key << 3) | (edge << 2) | label, into its region's bucket
+//              (block-local counting sort in shared memory; each flush's
+//              run appended to its bucket with one atomic);
 //   split   -- per region, order the events by 2048-slot table tile
 //              (units of events: histogram, offsets, counting-sorted scatter);
 //   apply   -- one CTA per tile: a bulk copy brings the tile into shared
@@ -20,12 +21,14 @@
 //   deferred -- the few events whose probe left their tile, from their home
 //              slot, with the global find-or-claim.
 // The earlier streaming apply (all CTAs sweep the region-ordered events with
-// global atomics inside an L2-resident window) remains as apply_mode = 1.
+// global atomics inside an L2-resident window) remains as apply_mode = 1; it
+// needs gap-free region ranges, so it keeps an exact count pass (histogram
+// per slice of tiles) and its scan ahead of the scatter.
 // The result is identical to the direct insert (additions commute).  Events
-// hold a key of at most 60 bits, so the binned path serves k <= 31.  The scan
-// checks that the events fit the handle's event buffer; if not, every later
-// binned kernel returns at once and the direct insert kernel, launched last
-// with the same flag as its gate, does the work instead.
+// hold a key of at most 60 bits, so the binned path serves k <= 31.  If the
+// buckets do not fit the handle's event buffer, or one of them fills up,
+// every later binned kernel returns at once and the direct insert kernel,
+// launched last with the same flag as its gate, does the work instead.
 #include <algorithm>
 
 #include "dbg_binned.cuh"
@@ -144,6 +147,84 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+// --- bucketed reservation (the tiled path's replacement of K1b/K1c) -----------
+//
+// The tiled apply re-partitions every region's events by tile, so it needs
+// each region's events together but not in an exact, gap-free range.  The
+// count pass can then go: each region gets a bucket of its expected events
+// (its share of the table's slots) with a margin, and the scatter appends
+// every flush's run to its bucket.  Regions are drawn by the hash per
+// distinct key, not per position, so a region's count varies with the keys'
+// multiplicities (about the coverage for genomic keys): its standard
+// deviation is sqrt(expected x mean squared multiplicity / mean multiplicity),
+// about 10^4 events for the 100 Mbp workload's 4-million-event regions.  The
+// margin, 3 % + 16 sqrt(expected) + 256, is several such deviations.  A
+// bucket that fills up anyway (inputs dominated by a few heavily repeated
+// keys) clears the use-binned flag, and the direct insert does the call
+// instead, exactly as when the events exceed the buffer.
+
+// *total = vertex positions of the read set, sum of max(0, len - k + 2).
+__global__ void k_bin_total(const uint64_t *offsets, uint64_t n_reads, int k,
+                            unsigned long long *total) {
+  unsigned long long v = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += stride) {
+    const uint64_t a = offsets[r], b = offsets[r + 1];
+    const uint64_t len = b > a ? b - a : 0;
+    v += len >= (uint64_t)k ? len - k + 2 : 0;
+  }
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
+// One CTA of 1024 threads (two regions each): bucket p starts at begin[p]
+// and holds its expected events plus the margin; cursor[p] = begin[p];
+// the flag says whether all buckets fit the buffer; resets the scatter's
+// slice counter.
+__global__ void __launch_bounds__(1024)
+    k_bin_buckets(const unsigned long long *total, uint64_t n_slots, int shift, int parts,
+                  unsigned long long *begin, unsigned long long *cursor, uint64_t cap,
+                  unsigned long long *ctr, uint32_t *use_binned) {
+  __shared__ unsigned long long s_warp[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double E = (double)*total;
+  auto bucket = [&](int p) -> unsigned long long {
+    if (p >= parts) return 0ull;
+    const uint64_t first = (uint64_t)p << shift;
+    const uint64_t slots = min((uint64_t)1 << shift, n_slots - first);
+    const double expected = E * (double)slots / (double)n_slots;
+    return (unsigned long long)ceil(expected * 1.03 + 16.0 * sqrt(expected) + 256.0);
+  };
+  const int p0 = 2 * tid;
+  const unsigned long long ca = bucket(p0), cb = bucket(p0 + 1);
+  const unsigned long long local = ca + cb;
+  unsigned long long incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = s_warp[lane];
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(kFull, w, d);
+      if (lane >= d) w += o;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  const unsigned long long b = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
+  if (p0 < parts) begin[p0] = cursor[p0] = b;
+  if (p0 + 1 < parts) begin[p0 + 1] = cursor[p0 + 1] = b + ca;
+  if (tid == 0) {
+    const unsigned long long all = s_warp[31];
+    begin[parts] = all;
+    *use_binned = all <= cap ? 1u : 0u;
+    ctr[1] = 0;
+  }
+}
+
 // --- K1d --------------------------------------------------------------------
 
 // A round of the tile walk gives every thread kRun events; each keeps them in
@@ -166,6 +247,10 @@ struct ScatterVisitor {
   uint64_t *out;
   uint64_t cap;  // events the buffer holds: never store past it
   int shift, parts;
+  // bucketed mode: runs are appended to per-region buckets at flush time
+  unsigned long long *bucket_cursor = nullptr;     // parts: next free position
+  const unsigned long long *bucket_end = nullptr;  // parts: end of each bucket
+  uint32_t *use_binned = nullptr;                  // cleared when a bucket overflows
   uint64_t ev[kRun];     // this thread's events of the round
   uint32_t where[kRun];  // region << 16 | rank, or ~0 for no event
 
@@ -212,8 +297,18 @@ struct ScatterVisitor {
     for (int p = p0; p < p1; ++p) {
       const uint32_t h = hist[p];
       off[p] = run;
-      gbase[p] = cur[p] - run;
-      cur[p] += h;
+      if (bucket_cursor == nullptr) {
+        gbase[p] = cur[p] - run;
+        cur[p] += h;
+      } else if (h) {
+        const unsigned long long at = atomicAdd(&bucket_cursor[p], (unsigned long long)h);
+        if (at + h > bucket_end[p]) {  // the bucket is full: the direct insert takes over
+          atomicExch(use_binned, 0u);
+          gbase[p] = ~0ull;
+        } else {
+          gbase[p] = at - run;
+        }
+      }
       run += h;
     }
     __syncthreads();
@@ -231,8 +326,9 @@ struct ScatterVisitor {
     __syncthreads();
     const uint32_t total = s_total;
     for (uint32_t j = tid; j < total; j += BLOCK) {
-      const unsigned long long at = gbase[spid[j]] + j;
-      if (at < cap) __stcs(out + at, sorted[j]);
+      const unsigned long long g = gbase[spid[j]];
+      const unsigned long long at = g + j;
+      if (g != ~0ull && at < cap) __stcs(out + at, sorted[j]);
     }
     __syncthreads();
     for (int p = tid; p < parts; p += BLOCK) hist[p] = 0;
@@ -250,7 +346,8 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
     k_bin_scatter(const __grid_constant__ ItemPack<1> pk, int tile_reads, int shift, int parts,
                   uint64_t slices, const uint32_t *hist, unsigned long long *cursor, uint64_t *out,
-                  uint64_t cap, unsigned long long *ctr, const uint32_t *use_binned) {
+                  uint64_t cap, unsigned long long *ctr, uint32_t *use_binned,
+                  const unsigned long long *bucket_end) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char *p = smem + tile_smem_bytes(tile_reads);
@@ -270,15 +367,22 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
   vis.cap = cap;
   vis.shift = shift;
   vis.parts = parts;
+  if (bucket_end != nullptr) {  // bucketed: no count pass, runs appended per flush
+    vis.bucket_cursor = cursor;
+    vis.bucket_end = bucket_end;
+    vis.use_binned = use_binned;
+  }
   const uint64_t T = pk.total_tiles;
   for (int q = threadIdx.x; q < parts; q += BLOCK) vis.hist[q] = 0;
   for (;;) {
     const uint64_t sl = grab(&ctr[1]);
     if (sl >= slices) break;
-    // reserve this slice's run in every region it reaches (counted by K1b)
-    for (int q = threadIdx.x; q < parts; q += BLOCK) {
-      const uint32_t h = hist[sl * parts + q];
-      vis.cur[q] = h ? atomicAdd(&cursor[q], (unsigned long long)h) : 0ull;
+    if (bucket_end == nullptr) {
+      // reserve this slice's run in every region it reaches (counted by K1b)
+      for (int q = threadIdx.x; q < parts; q += BLOCK) {
+        const uint32_t h = hist[sl * parts + q];
+        vis.cur[q] = h ? atomicAdd(&cursor[q], (unsigned long long)h) : 0ull;
+      }
     }
     __syncthreads();
     for_each_vertex<BLOCK, 1, kRun>(pk, tile_reads, smem, vis, sl * T / slices,
@@ -471,14 +575,21 @@ struct TileAux {
 };
 
 // unit_base[p] = units of regions < p, each region cut into ceil(count/unit) units.
+// (bucketed: a region's events are those its bucket received, cursor - begin;
+// they become the region counts the later passes read)
 __global__ void __launch_bounds__(1024)
-    k_tile_units(const unsigned long long *counts, int parts, uint64_t unit,
+    k_tile_units(unsigned long long *counts, const unsigned long long *begin,
+                 const unsigned long long *cursor, int bucketed, int parts, uint64_t unit,
                  unsigned long long *unit_base, unsigned long long *deferred,
                  const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   __shared__ unsigned long long s_warp[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int p0 = 2 * tid;
+  if (bucketed) {
+    if (p0 < parts) counts[p0] = cursor[p0] - begin[p0];
+    if (p0 + 1 < parts) counts[p0 + 1] = cursor[p0 + 1] - begin[p0 + 1];
+  }
   const unsigned long long ua = p0 < parts ? (counts[p0] + unit - 1) / unit : 0ull;
   const unsigned long long ub = p0 + 1 < parts ? (counts[p0 + 1] + unit - 1) / unit : 0ull;
   const unsigned long long local = ua + ub;
@@ -543,15 +654,15 @@ __device__ __forceinline__ void load_batch(const uint64_t *__restrict__ ev, uint
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     k_tile_count(const uint64_t *__restrict__ ev, const unsigned long long *begin,
-                 TileAux aux, int parts, uint64_t unit, int shift, int tpr, uint64_t n_slots,
-                 const uint32_t *use_binned) {
+                 const unsigned long long *counts, TileAux aux, int parts, uint64_t unit,
+                 int shift, int tpr, uint64_t n_slots, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   extern __shared__ uint32_t s_hist[];  // tpr
   const uint64_t n_units = aux.unit_base[parts];
   for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
     const int p = unit_region(aux.unit_base, parts, u);
     const uint64_t a = begin[p] + (u - aux.unit_base[p]) * unit;
-    const uint64_t b = min(a + unit, (uint64_t)begin[p + 1]);
+    const uint64_t b = min(a + unit, (uint64_t)(begin[p] + counts[p]));
     for (int j = threadIdx.x; j < tpr; j += BLOCK) s_hist[j] = 0u;
     __syncthreads();
     for (uint64_t base = a; base < b; base += (uint64_t)BLOCK * kBatch) {
@@ -637,8 +748,9 @@ constexpr size_t tile_scatter_smem(int tpr) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     k_tile_scatter(const uint64_t *__restrict__ ev, uint64_t *__restrict__ ev2,
-                   const unsigned long long *begin, TileAux aux, int parts, uint64_t unit,
-                   int shift, int tpr, uint64_t n_slots, const uint32_t *use_binned) {
+                   const unsigned long long *begin, const unsigned long long *counts, TileAux aux,
+                   int parts, uint64_t unit, int shift, int tpr, uint64_t n_slots,
+                   const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   constexpr int C = BLOCK * kBatch;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -655,7 +767,7 @@ __global__ void __launch_bounds__(BLOCK)
   for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
     const int p = unit_region(aux.unit_base, parts, u);
     const uint64_t a = begin[p] + (u - aux.unit_base[p]) * unit;
-    const uint64_t b = min(a + unit, (uint64_t)begin[p + 1]);
+    const uint64_t b = min(a + unit, (uint64_t)(begin[p] + counts[p]));
     const uint32_t *h = aux.unit_hist + u * (uint64_t)tpr;
     for (int j = tid; j < tpr; j += BLOCK) s_at[j] = h[j];
     uint64_t *out = ev2 + begin[p];
@@ -757,6 +869,7 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint64_t first,
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     k_tile_apply(const uint64_t *__restrict__ ev2, uint64_t *deferred_ev, TileAux aux,
+                 const unsigned long long *begin, const unsigned long long *counts, int tpr,
                  uint64_t n_tiles, Slot *table, uint64_t n_slots, uint32_t max_probes,
                  uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
                  unsigned long long *spill_count, const uint32_t *use_binned) {
@@ -773,7 +886,11 @@ __global__ void __launch_bounds__(BLOCK)
   __syncthreads();
   uint32_t parity = 0;
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const uint64_t a = aux.tile_begin[t], b = aux.tile_begin[t + 1];
+    // a region's last tile ends with the region's events (buckets may leave gaps)
+    const uint64_t p = t / (uint64_t)tpr;
+    const uint64_t a = aux.tile_begin[t];
+    const uint64_t b = (t + 1) % (uint64_t)tpr == 0 ? (uint64_t)(begin[p] + counts[p])
+                                                      : (uint64_t)aux.tile_begin[t + 1];
     const uint64_t first = t << kTileLog2;
     // no event, or a tile past the table's end (never has one): the tile stays
     // as it is (the same decision for the whole CTA)
@@ -883,7 +1000,8 @@ MetaView meta_view(dbg_handle h) {
 }
 
 int ensure_bin_scratch(dbg_handle h, uint64_t events) {
-  if (events == 0) events = std::max(kBinMinEvents, kBinEventsPerSlot * h->n_slots);
+  if (events == 0)
+    events = std::max(kBinMinEvents, kBinEventsPerSlot * h->n_slots + h->n_slots / 4);
   if (!h->bin_meta) {
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, kBinMetaBytes);
@@ -1017,7 +1135,8 @@ int launch_tile_scatter(dbg_handle h, const MetaView &mv, const TileAux &aux,
   int per_sm = 0;
   DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_scatter<BT>, BT, smem));
   k_tile_scatter<BT><<<std::max(1, per_sm) * sms, BT, smem, s>>>(
-      h->bin_ev, h->bin_ev2, mv.begin, aux, geo.parts, unit, geo.shift, tpr, h->n_slots, mv.flag);
+      h->bin_ev, h->bin_ev2, mv.begin, mv.counts, aux, geo.parts, unit, geo.shift, tpr,
+      h->n_slots, mv.flag);
   DBG_CK(cudaGetLastError());
   return DBG_OK;
 }
@@ -1049,10 +1168,21 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   DBG_CK(cudaStreamIsCapturing(s, &capture));
   const bool capturing = capture != cudaStreamCaptureStatusNone;
   if (!capturing) DBG_CK(cudaStreamWaitEvent(s, h->bin_done, 0));
+  const int tpr = 1 << std::max(0, geo.shift - kTileLog2);
+  // (unit starts are kept in 32 bits relative to their region: the event
+  // buffer must stay below 2^32 events)
+  const bool tiled = want_tiled && geo.shift >= kTileLog2 && tpr <= kMaxTilesPerRegion &&
+                     ensure_tile_scratch(h, geo, tpr, capturing);
   DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, geo.parts * sizeof(unsigned long long), s));
   timer_mark(h, call, 1, s);
-  {
+  if (tiled) {  // buckets instead of the count pass and its scan
+    k_bin_total<<<sms * 4, 256, 0, s>>>(it.offsets, it.n_reads, it.k, mv.ctr + 2);
+    DBG_CK(cudaGetLastError());
+    k_bin_buckets<<<1, 1024, 0, s>>>(mv.ctr + 2, h->n_slots, geo.shift, geo.parts, mv.begin,
+                                     mv.cursor, h->bin_cap, mv.ctr, mv.flag);
+    DBG_CK(cudaGetLastError());
+  } else {
     const size_t smem = tile_smem_bytes(tile_reads) + (size_t)geo.parts * 4;
     if (smem > 48 * 1024)
       DBG_CK(cudaFuncSetAttribute(k_bin_count<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1062,11 +1192,11 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     k_bin_count<B><<<grid, B, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices, mv.hist,
                                          mv.counts, mv.ctr);
     DBG_CK(cudaGetLastError());
+    timer_mark(h, call, 2, s);
+    k_bin_scan<<<1, 1024, 0, s>>>(mv.counts, geo.parts, mv.begin, mv.cursor, h->bin_cap, mv.ctr,
+                                  mv.flag);
+    DBG_CK(cudaGetLastError());
   }
-  timer_mark(h, call, 2, s);
-  k_bin_scan<<<1, 1024, 0, s>>>(mv.counts, geo.parts, mv.begin, mv.cursor, h->bin_cap, mv.ctr,
-                                mv.flag);
-  DBG_CK(cudaGetLastError());
   timer_mark(h, call, 3, s);
   {
     // 512 threads: flushes of 4096 events, so that a region's run in a flush
@@ -1079,21 +1209,17 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<BS>, BS, smem));
     const int grid = (int)std::min<uint64_t>(slices, (uint64_t)std::max(1, per_sm) * sms);
     k_bin_scatter<BS><<<grid, BS, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices, mv.hist,
-                                             mv.cursor, h->bin_ev, h->bin_cap, mv.ctr, mv.flag);
+                                             mv.cursor, h->bin_ev, h->bin_cap, mv.ctr, mv.flag,
+                                             tiled ? mv.begin + 1 : nullptr);
     DBG_CK(cudaGetLastError());
   }
-  const int tpr = 1 << std::max(0, geo.shift - kTileLog2);
-  // (unit starts are kept in 32 bits relative to their region: the event
-  // buffer must stay below 2^32 events)
-  const bool tiled = want_tiled && geo.shift >= kTileLog2 && tpr <= kMaxTilesPerRegion &&
-                     ensure_tile_scratch(h, geo, tpr, capturing);
   if (tiled) {
     const uint64_t unit = tile_unit(tpr);
     const TileAux aux = tile_aux(h, geo, tpr);
     const uint64_t n_tiles = (uint64_t)geo.parts * tpr;
     timer_mark(h, call, 4, s);
-    k_tile_units<<<1, 1024, 0, s>>>(mv.counts, geo.parts, unit, aux.unit_base, aux.deferred,
-                                    mv.flag);
+    k_tile_units<<<1, 1024, 0, s>>>(mv.counts, mv.begin, mv.cursor, 1, geo.parts, unit,
+                                    aux.unit_base, aux.deferred, mv.flag);
     DBG_CK(cudaGetLastError());
     {
       int per_sm = 0;
@@ -1102,7 +1228,8 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
       DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_count<B>, B,
                                                            (size_t)tpr * 4));
       k_tile_count<B><<<std::max(1, per_sm) * sms, B, (size_t)tpr * 4, s>>>(
-          h->bin_ev, mv.begin, aux, geo.parts, unit, geo.shift, tpr, h->n_slots, mv.flag);
+          h->bin_ev, mv.begin, mv.counts, aux, geo.parts, unit, geo.shift, tpr, h->n_slots,
+          mv.flag);
       DBG_CK(cudaGetLastError());
     }
     k_tile_offsets<B><<<geo.parts, B, 0, s>>>(mv.begin, aux, geo.parts, tpr, mv.flag);
@@ -1128,8 +1255,8 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
       DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_apply<BA>, BA, smem));
       const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)std::max(1, per_sm) * sms);
       k_tile_apply<BA><<<(int)grid, BA, smem, s>>>(
-          h->bin_ev2, h->bin_ev, aux, n_tiles, h->table, h->n_slots, h->max_probes, h->d_status,
-          h->d_spill, h->spill_cap, h->d_spill_count, mv.flag);
+          h->bin_ev2, h->bin_ev, aux, mv.begin, mv.counts, tpr, n_tiles, h->table, h->n_slots,
+          h->max_probes, h->d_status, h->d_spill, h->spill_cap, h->d_spill_count, mv.flag);
       DBG_CK(cudaGetLastError());
     }
     timer_mark(h, call, 6, s);

@@ -8,7 +8,8 @@ namespace dbg {
 constexpr int kBinMaxParts = 2048;           // regions of the table, at most
 constexpr uint64_t kBinMinTableBytes = 256ull << 20;  // auto mode: tables at least this big
 constexpr uint64_t kBinMinEvents = 16ull << 20;       // smallest event buffer
-constexpr uint64_t kBinEventsPerSlot = 4;             // default event buffer: 4 events per slot
+constexpr uint64_t kBinEventsPerSlot = 4;             // default event buffer: 4.25 events per slot
+                                                      // (4 + 1/4, the buckets' margin included)
 
 constexpr uint64_t kBinSlices = 4096;                // count/scatter work units, at most
 constexpr int kBinMinShift = 18;                     // automatic: regions of at least 2^18 slots (8 MiB)

@@ -470,6 +470,9 @@ extern "C" int dbg_reserve_events(dbg_handle h, uint64_t events) {
   if (!h) return DBG_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  // room for the buckets' margins (3 % and more per region) on top of the
+  // positions asked for
+  if (events > 0) events += events / 16 + 65536 + 256 * 2048;
   return dbg::ensure_bin_scratch(h, events);
 }
 

@@ -9,8 +9,12 @@ the shard's sorted export (uint64 keys, then uint32 [n, 4] counters, both
 little-endian).  A GPU export, split with :func:`oracle.shard_of_keys`,
 must reproduce every digest bit for bit.
 
-Usage: ``python tests/golden/make_golden.py [workload ...]`` (default: all
-three plain-build workloads; the 100 Mbp one takes tens of minutes).
+The batched workload (``batch256``: 256 samples of ``synth.batch_samples``)
+is recorded one digest per sample, unsharded.
+
+Usage: ``python tests/golden/make_golden.py [workload ...]`` (default: the
+three plain-build workloads and ``batch256``; the 100 Mbp one and the batch
+take tens of minutes each).
 """
 
 import hashlib
@@ -38,10 +42,40 @@ def digest(keys: np.ndarray, counts: np.ndarray) -> str:
     return h.hexdigest()
 
 
+def _sample_digest(job):
+    i, seed = job
+    rs = synth.batch_sample(i, seed)
+    g = oracle.build_graph(rs.packed, rs.offsets, rs.k, threads=1)
+    assert int(g.counts.astype(np.uint64).sum()) == rs.n_edges()
+    return i, {"k": rs.k, "n_reads": rs.n_reads, "n_edges": rs.n_edges(),
+               "n_vertices": g.n_vertices, "sha256": digest(g.keys, g.counts)}
+
+
+def batch(data, threads, n=256, seed=4):
+    """One oracle build per sample, the samples spread over worker processes."""
+    import multiprocessing as mp
+    t0 = time.time()
+    samples = [None] * n
+    with mp.get_context("spawn").Pool(threads) as pool:
+        for done, (i, rec) in enumerate(pool.imap_unordered(_sample_digest,
+                                                            [(i, seed) for i in range(n)])):
+            samples[i] = rec
+            if (done + 1) % 32 == 0:
+                print(f"batch256: {done + 1}/{n} samples ({time.time() - t0:.0f} s)", flush=True)
+    data["batch256"] = {
+        "seed": seed, "samples": samples,
+        "digest": "sha256 of little-endian uint64 keys then uint32 [n,4] counters, per sample",
+    }
+    json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
+
+
 def main(names):
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     threads = os.cpu_count() or 1
     for name in names:
+        if name == "batch256":
+            batch(data, threads)
+            continue
         t0 = time.time()
         rs = synth.WORKLOADS[name]()
         P = SHARDS[name]
@@ -67,4 +101,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(SHARDS))
+    main(sys.argv[1:] or list(SHARDS) + ["batch256"])

@@ -51,10 +51,11 @@ def test_binned_single_region_table():
 
 
 def test_binned_falls_back_when_events_do_not_fit():
-    rs = synth.ragged_reads(2000, 200, 21, 34)
+    rs = synth.ragged_reads(20000, 200, 21, 34)
     g = binned_graph(rs)
-    g.reserve_events(1000)  # far fewer than the vertex positions
-    assert g.info()["event_capacity"] == 1000
+    positions = int(np.maximum(rs.lengths() - rs.k + 2, 0).sum())
+    g.reserve_events(1000)  # far fewer than the vertex positions (plus the buckets' margin)
+    assert 1000 <= g.info()["event_capacity"] < positions
     packed, offsets = to_device(rs)
     g.insert(packed, offsets)
     assert g.status() == dbg.OK
@@ -124,7 +125,8 @@ def test_kernel_timer_records_the_kernels_each_path_launches():
     packed, offsets = to_device(rs)
     K = len(dbg.Graph.KERNELS)
     for tuning, launched in ((dict(insert_path=1), [0]),
-                             (dict(insert_path=2), [1, 2, 3, 4, 5, 6, 7]),
+                             # tiled: bucket sizing (under "bin_count") replaces count + scan
+                             (dict(insert_path=2), [1, 3, 4, 5, 6, 7]),
                              (dict(insert_path=2, apply_mode=1), [1, 2, 3, 5, 7])):
         g = dbg.Graph(rs.k, MULTI_REGION)
         g.set_tuning(**tuning)
@@ -192,4 +194,22 @@ def test_tiled_apply_respects_max_probes_with_a_spill():
         g.grow(4 * g.info()["n_slots"])
     assert g.status() == dbg.OK
     assert_same_graph(g.export(), exp)
+    g.close()
+
+
+def test_bucket_overflow_from_repeated_keys_falls_back_exactly():
+    # one read repeated many times puts most positions in few regions: a
+    # bucket (expected size + six standard deviations) overflows, and the
+    # direct insert does the call instead -- the same graph either way
+    rs = synth.from_strings(["ACGTTGCAAGGCTTAACCGTAGGCATCGATCGGATC" * 4] * 20000, 21)
+    exp = oracle_export(rs)
+    g = binned_graph(rs)
+    g.enable_kernel_timing(2)
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert g.status() == dbg.OK
+    assert_same_graph(g.export(), exp)
+    t = g.kernel_times()
+    fallback = dbg.Graph.KERNELS.index("direct_fallback")
+    assert t[-1, fallback] >= 0
     g.close()

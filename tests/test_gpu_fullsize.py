@@ -53,3 +53,45 @@ def test_full_size_workload_matches_oracle_digests(name):
         sel = sh == p
         assert int(sel.sum()) == gold["shards"][p]["n_vertices"], p
         assert digest(keys[sel], counts[sel]) == gold["shards"][p]["sha256"], p
+
+
+def test_batched_workload_matches_oracle_digests():
+    # the 256-sample batched workload in the benchmark's launch configuration:
+    # sizes from the capacity predictor, one batched insert replayed from a
+    # CUDA graph, exact event buffers for the binned samples
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    gold = json.load(open(GOLD)).get("batch256") if os.path.exists(GOLD) else None
+    if gold is None:
+        pytest.skip("no recorded oracle digests for batch256")
+    from paper_2401_02756_gb300.predictor import REG_STRIDE, CapacityPredictor
+    build.build()
+    samples = synth.batch_samples(len(gold["samples"]), seed=gold["seed"])
+    dev = [to_device(rs) for rs in samples]
+    pred = CapacityPredictor()
+    regs = torch.zeros(len(samples), REG_STRIDE, dtype=torch.int32, device="cuda")
+    dbg.sketch_batch([(rs.k, pk, of, regs[i]) for i, (rs, (pk, of)) in enumerate(zip(samples, dev))])
+    preds = pred.predict_registers(regs, len(samples))
+    graphs = [dbg.Graph(rs.k, pred.capacity(p)) for rs, p in zip(samples, preds)]
+    for rs, g in zip(samples, graphs):
+        if g.info()["table_bytes"] >= (256 << 20):
+            g.reserve_events(int(np.maximum(rs.lengths() - rs.k + 2, 0).sum()))
+    items = [(g, pk, of) for g, (pk, of) in zip(graphs, dev)]
+    dbg.insert_batch(items)  # allocates the binned samples' scratch
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=s):
+        dbg.insert_batch(items, s)
+    for g in graphs:
+        g.reset()
+    cg.replay()
+    torch.cuda.synchronize()
+    for i, (rs, g, want) in enumerate(zip(samples, graphs, gold["samples"])):
+        assert (rs.k, rs.n_edges()) == (want["k"], want["n_edges"]), i
+        assert g.status() == dbg.OK, i
+        keys, counts = g.export()
+        assert keys.size == want["n_vertices"], i
+        assert digest(keys, counts) == want["sha256"], i
+        g.close()
