@@ -310,6 +310,7 @@ struct ScatterVisitor {
         }
       }
       run += h;
+      hist[p] = 0;  // read by no one after this prefix: ready for the next round
     }
     __syncthreads();
     // counting sort of the registers into region order
@@ -330,9 +331,8 @@ struct ScatterVisitor {
       const unsigned long long at = g + j;
       if (g != ~0ull && at < cap) __stcs(out + at, sorted[j]);
     }
-    __syncthreads();
-    for (int p = tid; p < parts; p += BLOCK) hist[p] = 0;
-    __syncthreads();
+    // no barrier here: the next round only touches hist (already cleared)
+    // before its first barrier, and sorted / spid / gbase / s_total after it
   }
 };
 
