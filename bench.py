@@ -310,6 +310,7 @@ def run_ours(args):
     k2_ms = [a.elapsed_time(b) for a, b, c in ev]
     kt = g.kernel_times(K)
     g.enable_kernel_timing(0)
+    bin_counters = g.binned_counters()  # the last timed call's (after the timed region)
     st = g.status()
     if st != dbg.OK:
         raise RuntimeError(f"timed build failed: {dbg.STATUS_NAMES.get(st, st)}")
@@ -325,8 +326,9 @@ def run_ours(args):
         if col:
             kernels[name] = {"ms": statistics.mean(col), "launches_per_step": 1}
     tiled = "bin_split" in kernels
-    if tiled:  # the split mark spans four kernels: units, count, offsets, scatter
-        kernels["bin_split"]["launches_per_step"] = 4
+    if tiled:  # bucket sizing: total + buckets; split: units (tile buckets) + tile scatter
+        kernels["bin_count"]["launches_per_step"] = 2
+        kernels["bin_split"]["launches_per_step"] = 2
     kernel_bytes = {
         "direct": touches * SECTOR_RMW_BYTES + in_bytes,
         # tiled: the read offsets only (bucket sizing); streaming: the count pass reads the input
@@ -461,7 +463,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "insert_only_edges_per_s": edges / k1_mean_s,
             "insert_ms": {"mean": statistics.mean(k1_ms), "min": min(k1_ms), "max": max(k1_ms)},
-            "insert_path": "binned" if "bin_apply" in kernels else "direct",
+            "insert_path": ("direct" if "bin_apply" not in kernels else
+                            "binned" if bin_counters["binned"] else "binned, fell back to direct"),
+            "binned_counters": bin_counters,
             "kernels": kernels,
             "k2_init_ms": statistics.mean(k2_ms),
             "export_ms": export_ms,

@@ -138,8 +138,8 @@ int dbg_set_tuning(dbg_handle h, const dbg_tuning *t);
 /* Size the binned insert's event buffers for `events` vertex positions per
  * call, plus a margin for the per-region buckets (events / 16 + 589,824;
  * 0 = the default of 4.25 per table slot), allocating the first (8 bytes per
- * event) now; the tiled apply adds a second one of the same size on its
- * first call.  Read sets with more positions per slot than the buffer allows
+ * event) now; the tiled apply adds a second one, 1.125 times as large plus
+ * 2^20 events (room for its per-tile buckets), on its first call.  Read sets with more positions per slot than the buffer allows
  * (high coverage into a tight table) should reserve their position count,
  * sum over reads of max(0, length - k + 2); otherwise those calls take the
  * direct insert.  Synchronizes the device if the buffer grows.  Errors:
@@ -162,6 +162,15 @@ int dbg_enable_kernel_timing(dbg_handle h, int calls);
  * *n_calls receives the number of calls written (at most max_calls). */
 int dbg_kernel_times(dbg_handle h, float *out_ms, int max_calls, int *n_calls);
 
+/* Diagnostics of the last binned insert call on this handle (synchronizes
+ * the device first): out[0] = 1 if the binned kernels did the call's work, 0
+ * if the direct insert did it (the events did not fit the buffers, or none
+ * has run); out[1] = events whose probe sequence left their 2048-slot tile;
+ * out[2] = events that did not fit their tile's bucket.  Both kinds are
+ * applied by a global pass after the tiles; both are 0 for the streaming
+ * apply.  `out` is a HOST array of 3.  Errors: INVALID_ARG, CUDA. */
+int dbg_binned_counters(dbg_handle h, uint64_t *out);
+
 /* Fill *out with the handle's parameters. */
 int dbg_get_info(dbg_handle h, dbg_info *out);
 
@@ -182,7 +191,7 @@ int dbg_get_info(dbg_handle h, dbg_info *out);
  * crosses DRAM once in whole lines; events whose probe leaves their tile are
  * applied afterwards from their home slots.  It is chosen automatically for
  * tables of 256 MiB or more and needs event buffers owned by the handle
- * (default 4.25 events per slot, 16 bytes per event across its two buffers,
+ * (default 4.25 events per slot, 17 bytes per event across its two buffers,
  * allocated by the first call that needs them, or sized with
  * dbg_reserve_events).  A call with more vertex positions than the buffer
  * holds runs the direct kernel instead (decided on the device).  Binned calls

@@ -545,20 +545,30 @@ __global__ void __launch_bounds__(BLOCK)
 //
 // That needs the events grouped by tile.  The scatter pass grouped them by
 // region (2^shift slots = tiles_per_region tiles); a second, region-local
-// partition pass (split) orders each region's events by tile:
-//   units   -- each region's events are cut into units of `unit` events;
-//   count   -- per unit, a histogram over the region's tiles;
-//   offsets -- per region, the tiles' event ranges and each unit's place in
-//              every tile's range (a prefix over the units);
-//   scatter -- per unit, every event to its tile's range (second buffer).
-// A probe sequence that runs off the end of its tile (keys homed near the
-// end of a full stretch of slots) cannot continue there: the next tile
-// belongs to another CTA.  Such events are deferred to a list (in the first
-// event buffer, which the split pass has consumed) and applied afterwards,
-// from their home slot, with the direct insert's global find-or-claim; the
-// tile they would have spilled into is final by then.  A probe that reaches
-// max_probes inside its tile fails (or spills) exactly as in the direct
-// insert, so every key stays within max_probes of its home slot.
+// partition pass (split) groups each region's events by tile:
+//   units   -- one CTA: each region's event count, its units of `unit`
+//              events, and one bucket per tile of the region in the second
+//              buffer (the region's mean events per tile plus a margin), the
+//              buckets of all regions end to end and an overflow area after
+//              them;
+//   scatter -- per unit, every event appended to its tile's bucket: each
+//              chunk is counting-sorted by tile in shared memory, then each
+//              tile's run takes its place with one atomic; what no longer
+//              fits the bucket goes to the overflow area.
+// No pass counts the tiles' events beforehand: the buckets are sized from
+// the region counts alone, and a tile that receives more than its bucket
+// holds (a key with many copies) sends the rest to the overflow area.
+// Events in the overflow area, and events whose probe sequence runs off the
+// end of their tile (keys homed near the end of a full stretch of slots),
+// cannot be applied in the tile: the next tile belongs to another CTA.  They
+// are applied afterwards, from their home slot, with the direct insert's
+// global find-or-claim; the tiles are final by then.  The second kind are
+// listed in the first event buffer, which the split pass has consumed.  If
+// the overflow area fills up, the device flag turns the binned kernels off
+// and the direct insert does the call (nothing has touched the table yet).
+// A probe that reaches max_probes inside its tile fails (or spills) exactly
+// as in the direct insert, so every key stays within max_probes of its home
+// slot.
 
 constexpr int kTileLog2 = 11;
 constexpr int kTileSlots = 1 << kTileLog2;  // 2048 slots = 64 KB of shared memory
@@ -568,31 +578,19 @@ constexpr int kTiledShift = 20;             // automatic regions of the tiled pa
 constexpr int kBatch = 8;  // events each thread loads before it uses them (memory parallelism)
 
 struct TileAux {
-  uint32_t *unit_hist;            // [units][tpr] counts, then starts (relative to the region's)
-  unsigned long long *tile_begin; // [parts * tpr + 1]
-  unsigned long long *unit_base;  // [parts + 1]
-  unsigned long long *deferred;   // [1] events left for the global pass
+  unsigned long long *unit_base;    // [parts + 1] units of the regions before p
+  unsigned long long *region_base;  // [parts + 1] region p's first bucket; [parts]: overflow area
+  uint32_t *tile_cap;               // [parts] events one tile bucket of region p holds
+  uint32_t *fill;                   // [parts * tpr] events each tile received (zeroed per call)
+  unsigned long long *overflow;     // [1] events in the overflow area
+  unsigned long long *deferred;     // [1] events whose probe left their tile
 };
 
-// unit_base[p] = units of regions < p, each region cut into ceil(count/unit) units.
-// (bucketed: a region's events are those its bucket received, cursor - begin;
-// they become the region counts the later passes read)
-__global__ void __launch_bounds__(1024)
-    k_tile_units(unsigned long long *counts, const unsigned long long *begin,
-                 const unsigned long long *cursor, int bucketed, int parts, uint64_t unit,
-                 unsigned long long *unit_base, unsigned long long *deferred,
-                 const uint32_t *use_binned) {
-  if (ld_volatile_u32(use_binned) == 0u) return;
-  __shared__ unsigned long long s_warp[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int p0 = 2 * tid;
-  if (bucketed) {
-    if (p0 < parts) counts[p0] = cursor[p0] - begin[p0];
-    if (p0 + 1 < parts) counts[p0 + 1] = cursor[p0 + 1] - begin[p0 + 1];
-  }
-  const unsigned long long ua = p0 < parts ? (counts[p0] + unit - 1) / unit : 0ull;
-  const unsigned long long ub = p0 + 1 < parts ? (counts[p0 + 1] + unit - 1) / unit : 0ull;
-  const unsigned long long local = ua + ub;
+// Exclusive prefix over a CTA of 1024 threads; `total` receives the sum.
+__device__ __forceinline__ unsigned long long cta1024_exclusive_scan(unsigned long long local,
+                                                                     unsigned long long *s_warp,
+                                                                     unsigned long long &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long incl = local;
   for (int d = 1; d < 32; d <<= 1) {
     const unsigned long long o = __shfl_up_sync(kFull, incl, d);
@@ -609,12 +607,93 @@ __global__ void __launch_bounds__(1024)
     s_warp[lane] = w;
   }
   __syncthreads();
-  const unsigned long long b = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
-  if (p0 < parts) unit_base[p0] = b;
-  if (p0 + 1 < parts) unit_base[p0 + 1] = b + ua;
+  const unsigned long long ex = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
+  total = s_warp[31];
+  __syncthreads();  // s_warp is free again
+  return ex;
+}
+
+// One CTA of 1024 threads, two regions each.  Region p's events are those
+// its bucket received (cursor - begin); they become counts[p] and are cut
+// into ceil(count / unit) units (unit_base, a prefix).  The region's tiles
+// that lie inside the table (rt of them) get buckets of mean + slack events,
+// mean = count / rt, slack = 3 % + 16 sqrt(mean) + 64 (a tile's count varies
+// with its keys' multiplicities, as a region's does; at the 100 Mbp, 30x
+// workload 0.1 % of the events overflow).  If the buckets and an overflow area of 1/64 of the
+// buffer do not fit the buffer, the slack shrinks first, then the buckets.
+__global__ void __launch_bounds__(1024)
+    k_tile_units(unsigned long long *counts, const unsigned long long *begin,
+                 const unsigned long long *cursor, int parts, int shift, int tpr,
+                 uint64_t n_slots, uint64_t unit, uint64_t ev2_cap, TileAux aux,
+                 const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  __shared__ double s_red[3][32];
+  __shared__ unsigned long long s_warp[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long n[2];
+  uint32_t rt[2];
+  double mean[2], slack[2];
+  double sums[3] = {0.0, 0.0, 0.0};  // events, slack over all buckets, buckets
+  for (int i = 0; i < 2; ++i) {
+    const int p = 2 * tid + i;
+    n[i] = 0ull;
+    rt[i] = 0u;
+    mean[i] = slack[i] = 0.0;
+    if (p < parts) {
+      n[i] = cursor[p] - begin[p];
+      counts[p] = n[i];
+      const uint64_t left = (n_slots - ((uint64_t)p << shift) + kTileSlots - 1) >> kTileLog2;
+      rt[i] = (uint32_t)min((uint64_t)tpr, left);
+      if (n[i]) {
+        mean[i] = (double)n[i] / (double)rt[i];
+        slack[i] = 0.03 * mean[i] + 16.0 * sqrt(mean[i]) + 64.0;
+        sums[0] += (double)n[i];
+        sums[1] += slack[i] * (double)rt[i];
+        sums[2] += (double)rt[i];
+      }
+    }
+  }
+  for (int j = 0; j < 3; ++j) {
+    double v = sums[j];
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
+    if (lane == 0) s_red[j][warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = 0; j < 3; ++j) {
+      double v = s_red[j][lane];
+      for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
+      if (lane == 0) s_red[j][0] = v;
+    }
+  }
+  __syncthreads();
+  const double N = s_red[0][0], D = s_red[1][0], R = s_red[2][0];
+  const double avail = (double)(ev2_cap - ev2_cap / 64);
+  const double f = D > 0.0 ? fmin(1.0, fmax(0.0, (avail - N - R) / D)) : 0.0;
+  const double want = N + f * D;
+  const double g = want > avail ? avail / want : 1.0;
+  uint32_t cap[2];
+  for (int i = 0; i < 2; ++i) cap[i] = n[i] ? (uint32_t)floor((mean[i] + f * slack[i]) * g) : 0u;
+
+  const unsigned long long ua = (n[0] + unit - 1) / unit, ub = (n[1] + unit - 1) / unit;
+  unsigned long long units_total, buckets_total;
+  const unsigned long long u0 = cta1024_exclusive_scan(ua + ub, s_warp, units_total);
+  const unsigned long long sa = (unsigned long long)rt[0] * cap[0];
+  const unsigned long long sb = (unsigned long long)rt[1] * cap[1];
+  const unsigned long long b0 = cta1024_exclusive_scan(sa + sb, s_warp, buckets_total);
+  for (int i = 0; i < 2; ++i) {
+    const int p = 2 * tid + i;
+    if (p < parts) {
+      aux.unit_base[p] = u0 + (i ? ua : 0ull);
+      aux.region_base[p] = b0 + (i ? sa : 0ull);
+      aux.tile_cap[p] = cap[i];
+    }
+  }
   if (tid == 0) {
-    unit_base[parts] = s_warp[31];
-    *deferred = 0ull;
+    aux.unit_base[parts] = units_total;
+    aux.region_base[parts] = buckets_total;
+    *aux.overflow = 0ull;
+    *aux.deferred = 0ull;
   }
 }
 
@@ -650,185 +729,223 @@ __device__ __forceinline__ void load_batch(const uint64_t *__restrict__ ev, uint
   }
 }
 
-// Per unit: histogram of its events over the region's tiles.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    k_tile_count(const uint64_t *__restrict__ ev, const unsigned long long *begin,
-                 const unsigned long long *counts, TileAux aux, int parts, uint64_t unit,
-                 int shift, int tpr, uint64_t n_slots, const uint32_t *use_binned) {
-  if (ld_volatile_u32(use_binned) == 0u) return;
-  extern __shared__ uint32_t s_hist[];  // tpr
-  const uint64_t n_units = aux.unit_base[parts];
-  for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-    const int p = unit_region(aux.unit_base, parts, u);
-    const uint64_t a = begin[p] + (u - aux.unit_base[p]) * unit;
-    const uint64_t b = min(a + unit, (uint64_t)(begin[p] + counts[p]));
-    for (int j = threadIdx.x; j < tpr; j += BLOCK) s_hist[j] = 0u;
-    __syncthreads();
-    for (uint64_t base = a; base < b; base += (uint64_t)BLOCK * kBatch) {
-      uint64_t e[kBatch];
-      load_batch<BLOCK>(ev, base, b, e);
-#pragma unroll
-      for (int r = 0; r < kBatch; ++r)
-        if (e[r] != kEmpty) atomicAdd(&s_hist[tile_in_region(e[r], n_slots, shift, p)], 1u);
-    }
-    __syncthreads();
-    uint32_t *h = aux.unit_hist + u * (uint64_t)tpr;
-    for (int j = threadIdx.x; j < tpr; j += BLOCK) h[j] = s_hist[j];
-    __syncthreads();
-  }
-}
+// Per unit: every event appended to its tile's bucket in the second buffer.
+// Each chunk of BLOCK * kBatch events is counting-sorted by tile in shared
+// memory first, so that every tile's run of the chunk is written by
+// consecutive threads to consecutive addresses (coalesced stores instead of
+// one scattered 8-byte store per event) and takes its place in the bucket
+// with one atomic.  STAGED: a bulk copy brings the CTA's next chunk into
+// shared memory while the current one is sorted and written (the events'
+// load latency leaves the critical path); the 1024-thread form for large
+// regions has no room for the stage and loads to registers.
+constexpr int kMaxBinsPerThread = 4;  // tiles per region / tile scatter threads, at most
 
-// Per region (one CTA each): every tile's event range (tile_begin, absolute)
-// and, in unit_hist, where each unit's events of each tile start (relative
-// to the region's first event).
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    k_tile_offsets(const unsigned long long *begin, TileAux aux, int parts, int tpr,
-                   const uint32_t *use_binned) {
-  if (ld_volatile_u32(use_binned) == 0u) return;
-  __shared__ unsigned long long s_warp[BLOCK / 32];
-  const int p = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t u0 = aux.unit_base[p], u1 = aux.unit_base[p + 1];
-  unsigned long long *tb = aux.tile_begin + (uint64_t)p * tpr;
-  // each thread owns `per` consecutive tiles: their totals (kept in tb for now)
-  const int per = (tpr + BLOCK - 1) / BLOCK;
-  const int j0 = min(tpr, tid * per), j1 = min(tpr, j0 + per);
-  unsigned long long local = 0;
-  for (int j = j0; j < j1; ++j) {
-    unsigned long long total = 0;
-    for (uint64_t u = u0; u < u1; ++u) total += aux.unit_hist[u * (uint64_t)tpr + j];
-    tb[j] = total;
-    local += total;
-  }
-  unsigned long long incl = local;
-  for (int d = 1; d < 32; d <<= 1) {
-    const unsigned long long o = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += o;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned long long w = lane < BLOCK / 32 ? s_warp[lane] : 0ull;
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned long long o = __shfl_up_sync(kFull, w, d);
-      if (lane >= d) w += o;
-    }
-    if (lane < BLOCK / 32) s_warp[lane] = w;
-  }
-  __syncthreads();
-  // tile j's range starts after the events of the region's tiles < j
-  unsigned long long rel = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
-  for (int j = j0; j < j1; ++j) {
-    const unsigned long long total = tb[j];
-    tb[j] = begin[p] + rel;
-    unsigned long long at = rel;
-    for (uint64_t u = u0; u < u1; ++u) {
-      uint32_t *c = aux.unit_hist + u * (uint64_t)tpr + j;
-      const uint32_t n = *c;
-      *c = (uint32_t)at;
-      at += n;
-    }
-    rel += total;
-  }
-  if (p == parts - 1 && tid == 0) aux.tile_begin[(uint64_t)parts * tpr] = begin[parts];
-}
-
-// Per unit: every event to its tile's range in the second buffer.  Each
-// chunk of BLOCK * kBatch events is counting-sorted by tile in shared memory
-// first, so that every tile's run of the chunk is written by consecutive
-// threads to consecutive addresses (coalesced stores instead of one scattered
-// 8-byte store per event).
-template <int BLOCK>
+template <int BLOCK, bool STAGED>
 constexpr size_t tile_scatter_smem(int tpr) {
-  return (size_t)BLOCK * kBatch * (8 + 4) + (size_t)tpr * 12;
+  return (size_t)BLOCK * kBatch * (8 + 4) + (STAGED ? ((size_t)BLOCK * kBatch + 2) * 8 : 0) +
+         (size_t)tpr * 20;
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    k_tile_scatter(const uint64_t *__restrict__ ev, uint64_t *__restrict__ ev2,
+// A CTA's chunks, in order: its units blockIdx.x, + gridDim.x, ..., each cut
+// into chunks [x, y) of at most C events of the unit's range [., b).
+struct TileChunk {
+  uint64_t u, x, y, b;
+  int p;  // region of unit u
+};
+
+// The first chunk of unit u (false past the last unit).  Units are never
+// empty; p_hint is a region at or before u's (the regions only grow along a
+// CTA's units, so the walk forward is short).
+__device__ __forceinline__ bool tile_chunk_first(uint64_t u, int p_hint, uint64_t C,
+                                                 const unsigned long long *begin,
+                                                 const unsigned long long *counts,
+                                                 const TileAux &aux, int parts, uint64_t unit,
+                                                 TileChunk &c) {
+  if (u >= aux.unit_base[parts]) return false;
+  int p = p_hint;
+  while (p + 1 < parts && aux.unit_base[p + 1] <= u) ++p;
+  c.u = u;
+  c.p = p;
+  c.x = begin[p] + (u - aux.unit_base[p]) * unit;
+  c.b = min(c.x + unit, (uint64_t)(begin[p] + counts[p]));
+  c.y = min(c.x + C, c.b);
+  return true;
+}
+
+// Bulk copy of events [x & ~1, y & ~1) (16-byte aligned ends) into the stage;
+// an odd last event is read from global memory by its thread.
+__device__ __forceinline__ void stage_chunk(uint64_t *stage, const uint64_t *ev, uint64_t x,
+                                            uint64_t y, uint64_t *bar) {
+  const uint64_t x0 = x & ~1ull, y1 = y & ~1ull;
+  const uint32_t bytes = y1 > x0 ? (uint32_t)((y1 - x0) * sizeof(uint64_t)) : 0u;
+  mbar_expect_tx(bar, bytes);  // (0 bytes: the phase completes with this arrival)
+  if (bytes) bulk_load(stage, ev + x0, bytes, bar);
+}
+
+template <int BLOCK, bool STAGED>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threads per SM
+    k_tile_scatter(const uint64_t *__restrict__ ev, uint64_t *__restrict__ ev2, uint64_t ev2_cap,
                    const unsigned long long *begin, const unsigned long long *counts, TileAux aux,
                    int parts, uint64_t unit, int shift, int tpr, uint64_t n_slots,
-                   const uint32_t *use_binned) {
+                   uint32_t *status, uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   constexpr int C = BLOCK * kBatch;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t *s_ev = reinterpret_cast<uint64_t *>(smem);       // C, in tile order
-  uint32_t *s_tile = reinterpret_cast<uint32_t *>(s_ev + C);  // C: tile of s_ev[i]
-  uint32_t *s_at = s_tile + C;                                // tpr: next start (unit cursor)
-  uint32_t *s_hist = s_at + tpr;                              // tpr: chunk counts
-  uint32_t *s_off = s_hist + tpr;                             // tpr: chunk prefix
+  uint64_t *s_ev = reinterpret_cast<uint64_t *>(smem);  // C, in tile order
+  uint64_t *s_stage = s_ev + C;                          // C + 2 (STAGED): the next chunk
+  uint32_t *s_tile = reinterpret_cast<uint32_t *>(s_stage + (STAGED ? C + 2 : 0));  // C
+  uint32_t *s_hist = s_tile + C;   // tpr: chunk counts
+  uint32_t *s_off = s_hist + tpr;  // tpr: chunk prefix
+  uint32_t *s_fit = s_off + tpr;   // tpr: events of the run that fit the bucket
+  uint32_t *s_at = s_fit + tpr;    // tpr: their place, relative to the region's first bucket
+  uint32_t *s_ovf = s_at + tpr;    // tpr: the rest's place in the overflow area (~0: none)
   __shared__ uint32_t s_warp[BLOCK / 32];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint32_t s_failed;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int per = (tpr + BLOCK - 1) / BLOCK;  // bins per thread in the prefix
   const int j0 = min(tpr, tid * per), j1 = min(tpr, j0 + per);
-  const uint64_t n_units = aux.unit_base[parts];
-  for (uint64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-    const int p = unit_region(aux.unit_base, parts, u);
-    const uint64_t a = begin[p] + (u - aux.unit_base[p]) * unit;
-    const uint64_t b = min(a + unit, (uint64_t)(begin[p] + counts[p]));
-    const uint32_t *h = aux.unit_hist + u * (uint64_t)tpr;
-    for (int j = tid; j < tpr; j += BLOCK) s_at[j] = h[j];
-    uint64_t *out = ev2 + begin[p];
-    for (uint64_t base = a; base < b; base += C) {
-      for (int j = tid; j < tpr; j += BLOCK) s_hist[j] = 0u;
-      __syncthreads();
-      uint64_t e[kBatch];
-      uint32_t where[kBatch];  // tile << 16 | rank (rank < C <= 65536)
-      load_batch<BLOCK>(ev, base, b, e);
+  const uint64_t over_base = aux.region_base[parts];
+  const uint64_t over_cap = ev2_cap > over_base ? ev2_cap - over_base : 0ull;
+  uint64_t *over = ev2 + over_base;
+  if (STAGED && tid == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+    s_failed = 0u;
+  }
+  TileChunk c;
+  bool have = tile_chunk_first(blockIdx.x, unit_region(aux.unit_base, parts, blockIdx.x), C,
+                               begin, counts, aux, parts, unit, c);
+  __syncthreads();
+  if (STAGED && have && tid == 0) stage_chunk(s_stage, ev, c.x, c.y, &s_bar);
+  uint32_t parity = 0;
+  while (have) {
+    const uint32_t cap = aux.tile_cap[c.p];
+    uint32_t *fill = aux.fill + (uint64_t)c.p * tpr;
+    uint64_t *out = ev2 + aux.region_base[c.p];
+    // (the previous chunk's write-out reads no s_hist: no barrier before this)
+    for (int j = tid; j < tpr; j += BLOCK) s_hist[j] = 0u;
+    __syncthreads();
+    uint64_t e[kBatch];
+    if constexpr (STAGED) {
+      const bool ok = mbar_wait(&s_bar, parity);
+      parity ^= 1u;
+      if (!ok) s_failed = 1u;
+      const uint64_t x0 = c.x & ~1ull, y1 = c.y & ~1ull;
 #pragma unroll
       for (int r = 0; r < kBatch; ++r) {
-        if (e[r] != kEmpty) {
-          const uint32_t t = tile_in_region(e[r], n_slots, shift, p);
-          where[r] = (t << 16) | atomicAdd(&s_hist[t], 1u);
-        }
+        const uint64_t i = c.x + (uint64_t)r * BLOCK + tid;
+        e[r] = ok && i < c.y ? (i < y1 ? s_stage[i - x0] : __ldcs(ev + i)) : kEmpty;
       }
-      __syncthreads();
-      // exclusive prefix of the chunk's tile counts
-      uint32_t local = 0;
-      for (int j = j0; j < j1; ++j) local += s_hist[j];
-      uint32_t incl = local;
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += o;
-      }
-      if (lane == 31) s_warp[warp] = incl;
-      __syncthreads();
-      if (warp == 0) {
-        uint32_t w = lane < BLOCK / 32 ? s_warp[lane] : 0u;
-        for (int d = 1; d < 32; d <<= 1) {
-          const uint32_t o = __shfl_up_sync(kFull, w, d);
-          if (lane >= d) w += o;
-        }
-        if (lane < BLOCK / 32) s_warp[lane] = w;
-      }
-      __syncthreads();
-      uint32_t run = incl - local + (warp > 0 ? s_warp[warp - 1] : 0u);
-      for (int j = j0; j < j1; ++j) {
-        s_off[j] = run;
-        run += s_hist[j];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < kBatch; ++r) {
-        if (e[r] != kEmpty) {
-          const uint32_t t = where[r] >> 16;
-          const uint32_t i = s_off[t] + (where[r] & 0xFFFFu);
-          s_ev[i] = e[r];
-          s_tile[i] = t;
-        }
-      }
-      __syncthreads();
-      const uint32_t n = (uint32_t)min((uint64_t)C, b - base);
-      for (uint32_t i = tid; i < n; i += BLOCK) {
-        const uint32_t t = s_tile[i];
-        out[s_at[t] + (i - s_off[t])] = s_ev[i];
-      }
-      __syncthreads();
-      for (int j = tid; j < tpr; j += BLOCK) s_at[j] += s_hist[j];
-      __syncthreads();
+    } else {
+      load_batch<BLOCK>(ev, c.x, c.y, e);
     }
+    uint32_t where[kBatch];  // tile << 16 | rank (rank < C <= 65536)
+#pragma unroll
+    for (int r = 0; r < kBatch; ++r) {
+      if (e[r] != kEmpty) {
+        const uint32_t t = tile_in_region(e[r], n_slots, shift, c.p);
+        where[r] = (t << 16) | atomicAdd(&s_hist[t], 1u);
+      }
+    }
+    __syncthreads();  // (the stage is read: it may take the next chunk)
+    TileChunk nx = c;
+    bool have_next;
+    if (c.y < c.b) {
+      nx.x = c.y;
+      nx.y = min(nx.x + (uint64_t)C, c.b);
+      have_next = true;
+    } else {
+      have_next = tile_chunk_first(c.u + gridDim.x, c.p, C, begin, counts, aux, parts, unit, nx);
+    }
+    if constexpr (STAGED) {
+      if (s_failed) {  // a copy never landed: report it, let the direct insert do the call
+        if (tid == 0) {
+          set_sticky(status, DBG_ERR_TIMEOUT);
+          atomicExch(use_binned, 0u);
+          mbar_wait(&s_bar, parity ^ 1u);  // one more bounded chance for the copy to land
+        }
+        return;
+      }
+      if (have_next && tid == 0) stage_chunk(s_stage, ev, nx.x, nx.y, &s_bar);
+    }
+    // each run takes its place in its bucket; the atomics are issued first,
+    // so that their round trips overlap the prefix below
+    uint32_t got[kMaxBinsPerThread];
+#pragma unroll
+    for (int q = 0; q < kMaxBinsPerThread; ++q) {
+      const int j = j0 + q;
+      const uint32_t h = j < j1 ? s_hist[j] : 0u;
+      got[q] = h ? atomicAdd(&fill[j], h) : 0u;
+    }
+    // exclusive prefix of the chunk's tile counts
+    uint32_t local = 0;
+    for (int j = j0; j < j1; ++j) local += s_hist[j];
+    uint32_t incl = local;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += o;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < BLOCK / 32 ? s_warp[lane] : 0u;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, w, d);
+        if (lane >= d) w += o;
+      }
+      if (lane < BLOCK / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = incl - local + (warp > 0 ? s_warp[warp - 1] : 0u);
+#pragma unroll
+    for (int q = 0; q < kMaxBinsPerThread; ++q) {
+      const int j = j0 + q;
+      if (j >= j1) break;
+      const uint32_t h = s_hist[j];
+      s_off[j] = run;
+      run += h;
+      if (h) {
+        const uint32_t at = got[q];
+        const uint32_t fit = at >= cap ? 0u : min(h, cap - at);
+        s_fit[j] = fit;
+        s_at[j] = (uint32_t)((uint64_t)j * cap + at);
+        if (fit < h) {
+          const unsigned long long o = atomicAdd(aux.overflow, (unsigned long long)(h - fit));
+          if (o + (h - fit) > over_cap) {  // the area is full: the direct insert takes over
+            atomicExch(use_binned, 0u);
+            s_ovf[j] = ~0u;
+          } else {
+            s_ovf[j] = (uint32_t)o;
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kBatch; ++r) {
+      if (e[r] != kEmpty) {
+        const uint32_t t = where[r] >> 16;
+        const uint32_t i = s_off[t] + (where[r] & 0xFFFFu);
+        s_ev[i] = e[r];
+        s_tile[i] = t;
+      }
+    }
+    __syncthreads();
+    const uint32_t n = (uint32_t)(c.y - c.x);
+    for (uint32_t i = tid; i < n; i += BLOCK) {
+      const uint32_t t = s_tile[i];
+      const uint32_t r = i - s_off[t];
+      const uint32_t fit = s_fit[t];
+      if (r < fit) {
+        out[(uint64_t)s_at[t] + r] = s_ev[i];
+      } else {
+        const uint32_t o = s_ovf[t];
+        if (o != ~0u) over[(uint64_t)o + (r - fit)] = s_ev[i];
+      }
+    }
+    c = nx;
+    have = have_next;
   }
 }
 
@@ -868,8 +985,7 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint64_t first,
 // a bulk copy writes the tile back while the CTA moves to its next tile.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-    k_tile_apply(const uint64_t *__restrict__ ev2, uint64_t *deferred_ev, TileAux aux,
-                 const unsigned long long *begin, const unsigned long long *counts, int tpr,
+    k_tile_apply(const uint64_t *__restrict__ ev2, uint64_t *deferred_ev, TileAux aux, int tpr,
                  uint64_t n_tiles, Slot *table, uint64_t n_slots, uint32_t max_probes,
                  uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
                  unsigned long long *spill_count, const uint32_t *use_binned) {
@@ -886,11 +1002,11 @@ __global__ void __launch_bounds__(BLOCK)
   __syncthreads();
   uint32_t parity = 0;
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    // a region's last tile ends with the region's events (buckets may leave gaps)
+    // the tile's bucket: its events up to the bucket's size (the rest overflowed)
     const uint64_t p = t / (uint64_t)tpr;
-    const uint64_t a = aux.tile_begin[t];
-    const uint64_t b = (t + 1) % (uint64_t)tpr == 0 ? (uint64_t)(begin[p] + counts[p])
-                                                      : (uint64_t)aux.tile_begin[t + 1];
+    const uint32_t cap = aux.tile_cap[p];
+    const uint64_t a = aux.region_base[p] + (t - p * (uint64_t)tpr) * cap;
+    const uint64_t b = a + min(aux.fill[t], cap);
     const uint64_t first = t << kTileLog2;
     // no event, or a tile past the table's end (never has one): the tile stays
     // as it is (the same decision for the whole CTA)
@@ -938,16 +1054,20 @@ __global__ void __launch_bounds__(BLOCK)
   if (threadIdx.x == 0) bulk_wait_all();
 }
 
-// The deferred events, from their home slots, with the global find-or-claim.
-__global__ void k_tile_deferred(const uint64_t *__restrict__ deferred_ev, TileAux aux,
+// The events that left their tile, then those of the overflow area, from
+// their home slots, with the global find-or-claim.
+__global__ void k_tile_deferred(const uint64_t *__restrict__ deferred_ev,
+                                const uint64_t *__restrict__ ev2, TileAux aux, int parts,
                                 Slot *table, uint64_t n_slots, uint32_t max_probes,
                                 uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
                                 unsigned long long *spill_count, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
-  const uint64_t n = *aux.deferred;
+  const uint64_t nd = *aux.deferred;
+  const uint64_t n = nd + *aux.overflow;  // (all of it written: the flag is still set)
+  const uint64_t *over = ev2 + aux.region_base[parts];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint64_t e = deferred_ev[i];
+    const uint64_t e = i < nd ? deferred_ev[i] : over[i - nd];
     const unsigned long long key = e >> 3;
     uint64_t s;
     if (find_or_claim(table, n_slots, max_probes, key, s)) {
@@ -1031,31 +1151,40 @@ namespace {
 
 uint64_t tile_unit(int tpr) { return std::max<uint64_t>(16384, 64ull * (uint64_t)tpr); }
 
+// Events the second buffer holds: the first buffer's capacity plus room for
+// the tile buckets' margins (the first buffer's regions have their own);
+// bucket positions are 32-bit.
+uint64_t ev2_capacity(uint64_t bin_cap) {
+  return std::min<uint64_t>(bin_cap + bin_cap / 8 + (1ull << 20), 0xFFFFFFFFull);
+}
+
 // Layout of the tiled apply's aux buffer for a geometry.
 struct TileAuxLayout {
-  size_t hist, tile_begin, unit_base, deferred, total;
+  size_t unit_base, region_base, tile_cap, fill, counters, total;
 };
 
-TileAuxLayout tile_aux_layout(uint64_t bin_cap, const BinGeometry &geo, int tpr) {
+TileAuxLayout tile_aux_layout(const BinGeometry &geo, int tpr) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const uint64_t max_units = bin_cap / tile_unit(tpr) + (uint64_t)geo.parts;
   TileAuxLayout l;
-  l.hist = 0;
-  l.tile_begin = al(l.hist + max_units * (uint64_t)tpr * 4);
-  l.unit_base = al(l.tile_begin + ((uint64_t)geo.parts * tpr + 1) * 8);
-  l.deferred = al(l.unit_base + ((uint64_t)geo.parts + 1) * 8);
-  l.total = al(l.deferred + 8);
+  l.unit_base = 0;
+  l.region_base = al(l.unit_base + ((size_t)geo.parts + 1) * 8);
+  l.tile_cap = al(l.region_base + ((size_t)geo.parts + 1) * 8);
+  l.fill = al(l.tile_cap + (size_t)geo.parts * 4);
+  l.counters = al(l.fill + (size_t)geo.parts * tpr * 4);
+  l.total = al(l.counters + 16);
   return l;
 }
 
 TileAux tile_aux(dbg_handle h, const BinGeometry &geo, int tpr) {
-  const TileAuxLayout l = tile_aux_layout(h->bin_cap, geo, tpr);
+  const TileAuxLayout l = tile_aux_layout(geo, tpr);
   char *b = static_cast<char *>(h->bin_aux);
   TileAux a;
-  a.unit_hist = reinterpret_cast<uint32_t *>(b + l.hist);
-  a.tile_begin = reinterpret_cast<unsigned long long *>(b + l.tile_begin);
   a.unit_base = reinterpret_cast<unsigned long long *>(b + l.unit_base);
-  a.deferred = reinterpret_cast<unsigned long long *>(b + l.deferred);
+  a.region_base = reinterpret_cast<unsigned long long *>(b + l.region_base);
+  a.tile_cap = reinterpret_cast<uint32_t *>(b + l.tile_cap);
+  a.fill = reinterpret_cast<uint32_t *>(b + l.fill);
+  a.overflow = reinterpret_cast<unsigned long long *>(b + l.counters);
+  a.deferred = a.overflow + 1;
   return a;
 }
 
@@ -1063,13 +1192,13 @@ TileAux tile_aux(dbg_handle h, const BinGeometry &geo, int tpr) {
 // the streaming apply is used) if they cannot be had -- out of memory, or
 // inside a stream capture that began before they existed.
 bool ensure_tile_scratch(dbg_handle h, const BinGeometry &geo, int tpr, bool capturing) {
-  const size_t need = tile_aux_layout(h->bin_cap, geo, tpr).total;
+  const size_t need = tile_aux_layout(geo, tpr).total;
   if (h->bin_ev2 && h->bin_aux && h->bin_aux_bytes >= need) return true;
   if (capturing) return false;
   if (cudaDeviceSynchronize() != cudaSuccess) return false;  // earlier calls may use them
   if (!h->bin_ev2) {
     void *p = nullptr;
-    if (cudaMalloc(&p, h->bin_cap * sizeof(uint64_t)) != cudaSuccess) {
+    if (cudaMalloc(&p, ev2_capacity(h->bin_cap) * sizeof(uint64_t)) != cudaSuccess) {
       cudaGetLastError();  // clear the allocation failure
       return false;
     }
@@ -1125,18 +1254,20 @@ int launch_apply_m(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int
   }
 }
 
-template <int BT>
+template <int BT, bool STAGED>
 int launch_tile_scatter(dbg_handle h, const MetaView &mv, const TileAux &aux,
                         const BinGeometry &geo, uint64_t unit, int tpr, int sms, cudaStream_t s) {
-  const size_t smem = tile_scatter_smem<BT>(tpr);
+  if (tpr > kMaxBinsPerThread * BT) return DBG_ERR_INVALID_ARG;  // (the launch sizes BT by tpr)
+  const size_t smem = tile_scatter_smem<BT, STAGED>(tpr);
   // (set even below 48 KB: the kernel's static shared memory counts too)
-  DBG_CK(cudaFuncSetAttribute(k_tile_scatter<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem));
+  DBG_CK(cudaFuncSetAttribute(k_tile_scatter<BT, STAGED>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_scatter<BT>, BT, smem));
-  k_tile_scatter<BT><<<std::max(1, per_sm) * sms, BT, smem, s>>>(
-      h->bin_ev, h->bin_ev2, mv.begin, mv.counts, aux, geo.parts, unit, geo.shift, tpr,
-      h->n_slots, mv.flag);
+  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_scatter<BT, STAGED>, BT,
+                                                       smem));
+  k_tile_scatter<BT, STAGED><<<std::max(1, per_sm) * sms, BT, smem, s>>>(
+      h->bin_ev, h->bin_ev2, ev2_capacity(h->bin_cap), mv.begin, mv.counts, aux, geo.parts, unit,
+      geo.shift, tpr, h->n_slots, h->d_status, mv.flag);
   DBG_CK(cudaGetLastError());
   return DBG_OK;
 }
@@ -1169,12 +1300,18 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   const bool capturing = capture != cudaStreamCaptureStatusNone;
   if (!capturing) DBG_CK(cudaStreamWaitEvent(s, h->bin_done, 0));
   const int tpr = 1 << std::max(0, geo.shift - kTileLog2);
-  // (unit starts are kept in 32 bits relative to their region: the event
-  // buffer must stay below 2^32 events)
+  // (bucket positions are kept in 32 bits: the event buffer must stay below
+  // 2^32 events)
   const bool tiled = want_tiled && geo.shift >= kTileLog2 && tpr <= kMaxTilesPerRegion &&
                      ensure_tile_scratch(h, geo, tpr, capturing);
   DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, geo.parts * sizeof(unsigned long long), s));
+  h->bin_counters = nullptr;
+  if (tiled) {  // the tile buckets' fill counts
+    const TileAux aux = tile_aux(h, geo, tpr);
+    DBG_CK(cudaMemsetAsync(aux.fill, 0, (size_t)geo.parts * tpr * 4, s));
+    h->bin_counters = aux.overflow;
+  }
   timer_mark(h, call, 1, s);
   if (tiled) {  // buckets instead of the count pass and its scan
     k_bin_total<<<sms * 4, 256, 0, s>>>(it.offsets, it.n_reads, it.k, mv.ctr + 2);
@@ -1218,30 +1355,17 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     const TileAux aux = tile_aux(h, geo, tpr);
     const uint64_t n_tiles = (uint64_t)geo.parts * tpr;
     timer_mark(h, call, 4, s);
-    k_tile_units<<<1, 1024, 0, s>>>(mv.counts, mv.begin, mv.cursor, 1, geo.parts, unit,
-                                    aux.unit_base, aux.deferred, mv.flag);
-    DBG_CK(cudaGetLastError());
-    {
-      int per_sm = 0;
-      DBG_CK(cudaFuncSetAttribute(k_tile_count<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tpr * 4));
-      DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_count<B>, B,
-                                                           (size_t)tpr * 4));
-      k_tile_count<B><<<std::max(1, per_sm) * sms, B, (size_t)tpr * 4, s>>>(
-          h->bin_ev, mv.begin, mv.counts, aux, geo.parts, unit, geo.shift, tpr, h->n_slots,
-          mv.flag);
-      DBG_CK(cudaGetLastError());
-    }
-    k_tile_offsets<B><<<geo.parts, B, 0, s>>>(mv.begin, aux, geo.parts, tpr, mv.flag);
+    k_tile_units<<<1, 1024, 0, s>>>(mv.counts, mv.begin, mv.cursor, geo.parts, geo.shift, tpr,
+                                    h->n_slots, unit, ev2_capacity(h->bin_cap), aux, mv.flag);
     DBG_CK(cudaGetLastError());
     // chunks of 8 events per thread: larger blocks for more tiles per region,
     // so that each tile's run in a chunk stays several events long
     if (tpr <= 256) {
-      DBG_TRY(launch_tile_scatter<256>(h, mv, aux, geo, unit, tpr, sms, s));
+      DBG_TRY((launch_tile_scatter<256, true>(h, mv, aux, geo, unit, tpr, sms, s)));
     } else if (tpr <= 512) {
-      DBG_TRY(launch_tile_scatter<512>(h, mv, aux, geo, unit, tpr, sms, s));
+      DBG_TRY((launch_tile_scatter<512, true>(h, mv, aux, geo, unit, tpr, sms, s)));
     } else {
-      DBG_TRY(launch_tile_scatter<1024>(h, mv, aux, geo, unit, tpr, sms, s));
+      DBG_TRY((launch_tile_scatter<1024, false>(h, mv, aux, geo, unit, tpr, sms, s)));
     }
     timer_mark(h, call, 5, s);
     {
@@ -1255,14 +1379,14 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
       DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_apply<BA>, BA, smem));
       const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)std::max(1, per_sm) * sms);
       k_tile_apply<BA><<<(int)grid, BA, smem, s>>>(
-          h->bin_ev2, h->bin_ev, aux, mv.begin, mv.counts, tpr, n_tiles, h->table, h->n_slots,
-          h->max_probes, h->d_status, h->d_spill, h->spill_cap, h->d_spill_count, mv.flag);
+          h->bin_ev2, h->bin_ev, aux, tpr, n_tiles, h->table, h->n_slots, h->max_probes,
+          h->d_status, h->d_spill, h->spill_cap, h->d_spill_count, mv.flag);
       DBG_CK(cudaGetLastError());
     }
     timer_mark(h, call, 6, s);
-    k_tile_deferred<<<sms * 4, 256, 0, s>>>(h->bin_ev, aux, h->table, h->n_slots, h->max_probes,
-                                            h->d_status, h->d_spill, h->spill_cap,
-                                            h->d_spill_count, mv.flag);
+    k_tile_deferred<<<sms * 4, 256, 0, s>>>(h->bin_ev, h->bin_ev2, aux, geo.parts, h->table,
+                                            h->n_slots, h->max_probes, h->d_status, h->d_spill,
+                                            h->spill_cap, h->d_spill_count, mv.flag);
     DBG_CK(cudaGetLastError());
   } else {
     timer_mark(h, call, 5, s);
@@ -1278,6 +1402,22 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   if (st != DBG_OK) return st;
   timer_mark(h, call, 8, s);
   if (!capturing) DBG_CK(cudaEventRecord(h->bin_done, s));
+  return DBG_OK;
+}
+
+int binned_counters(dbg_handle h, uint64_t *out) {
+  out[0] = out[1] = out[2] = 0;
+  if (!h->bin_meta) return DBG_OK;  // no binned call yet
+  DBG_CK(cudaDeviceSynchronize());
+  uint32_t flag = 0;
+  DBG_CK(cudaMemcpy(&flag, meta_view(h).flag, sizeof(flag), cudaMemcpyDeviceToHost));
+  out[0] = flag != 0u;
+  if (flag && h->bin_counters) {
+    unsigned long long c[2] = {0ull, 0ull};  // overflow, deferred
+    DBG_CK(cudaMemcpy(c, h->bin_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    out[1] = c[1];
+    out[2] = c[0];
+  }
   return DBG_OK;
 }
 

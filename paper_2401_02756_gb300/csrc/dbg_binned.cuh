@@ -42,4 +42,9 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events);
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
                   cudaStream_t s, int call);
 
+// The last binned call's counters (synchronizes the device): out[0] = 1 if
+// the binned kernels did its work, out[1] = events whose probe left their
+// tile, out[2] = events that overflowed their tile's bucket.
+int binned_counters(dbg_handle h, uint64_t *out);
+
 }  // namespace dbg

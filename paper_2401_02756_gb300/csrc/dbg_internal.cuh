@@ -203,7 +203,9 @@ struct dbg_graph {
   uint64_t *bin_ev = nullptr;               // events, 8 bytes each
   uint64_t bin_cap = 0;                     // capacity in events
   uint64_t *bin_ev2 = nullptr;              // tiled apply: events again, grouped by table tile
-  void *bin_aux = nullptr;                  // tiled apply: unit histograms, tile ranges, counters
+  void *bin_aux = nullptr;                  // tiled apply: units, tile buckets, counters
+  unsigned long long *bin_counters = nullptr;  // the last binned call's overflow and deferred
+                                               // counts (tiled apply; null otherwise)
   uint64_t bin_aux_bytes = 0;
   unsigned long long *bin_meta = nullptr;   // region counts, ranges, cursors, flag
   cudaEvent_t bin_done = nullptr;           // orders binned calls that share the scratch

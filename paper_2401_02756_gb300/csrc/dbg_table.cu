@@ -466,6 +466,13 @@ extern "C" int dbg_kernel_times(dbg_handle h, float *out_ms, int max_calls, int 
   return DBG_OK;
 }
 
+extern "C" int dbg_binned_counters(dbg_handle h, uint64_t *out) {
+  if (!h || !out) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  return dbg::binned_counters(h, out);
+}
+
 extern "C" int dbg_reserve_events(dbg_handle h, uint64_t events) {
   if (!h) return DBG_ERR_INVALID_ARG;
   DeviceGuard g(h->device);

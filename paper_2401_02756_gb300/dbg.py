@@ -27,7 +27,8 @@ NOALLOC_EXPORT_MAX_VERTICES = 1 << 19
 
 EXPORTED = [
     "dbg_create", "dbg_create_ex", "dbg_table_bytes", "dbg_create_on", "dbg_destroy", "dbg_reset", "dbg_set_tuning", "dbg_get_info",
-    "dbg_reserve_events", "dbg_enable_kernel_timing", "dbg_kernel_times", "dbg_set_spill",
+    "dbg_reserve_events", "dbg_enable_kernel_timing", "dbg_kernel_times", "dbg_binned_counters",
+    "dbg_set_spill",
     "dbg_grow",
     "dbg_insert_reads", "dbg_insert_reads_host", "dbg_insert_batch", "dbg_get_status", "dbg_stats",
     "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_normalize", "dbg_find_contigs", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
@@ -101,6 +102,7 @@ def load() -> ctypes.CDLL:
         "dbg_grow": (I, [P, U64, P]),
         "dbg_enable_kernel_timing": (I, [P, I]),
         "dbg_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(I)]),
+        "dbg_binned_counters": (I, [P, ctypes.POINTER(U64)]),
         "dbg_insert_reads": (I, [P, P, P, U64, P]),
         "dbg_insert_reads_host": (I, [P, P, P, U64, P]),
         "dbg_insert_batch": (I, [ctypes.POINTER(BatchItem), I, P]),
@@ -275,6 +277,15 @@ class Graph:
         _check(load().dbg_kernel_times(self.handle, buf, max_calls, ctypes.byref(n)),
                "dbg_kernel_times")
         return np.frombuffer(buf, dtype=np.float32)[: K * n.value].reshape(n.value, K).copy()
+
+    def binned_counters(self) -> dict:
+        """The last binned insert call's diagnostics (synchronizes the device):
+        whether the binned kernels did its work, and how many events the
+        global pass applied -- those whose probe left their tile (deferred)
+        and those that did not fit their tile's bucket (overflow)."""
+        out = (ctypes.c_uint64 * 3)()
+        _check(load().dbg_binned_counters(self.handle, out), "dbg_binned_counters")
+        return {"binned": bool(out[0]), "deferred": int(out[1]), "overflow": int(out[2])}
 
     def set_spill(self, records: int) -> None:
         """Keep vertices that find no slot in a spill buffer of ``records``

@@ -37,6 +37,8 @@ def test_binned_matches_oracle(k):
     assert g.status() == dbg.OK
     if k <= 31:
         assert g.info()["event_capacity"] > 0
+    if k >= 21:  # (k = 2, 5: a handful of keys overflow a region's bucket: direct insert)
+        assert g.binned_counters()["binned"] == (k <= 31)  # 64-bit events need k <= 31
     assert_same_graph(g.export(), oracle_export(rs))
     g.close()
 
@@ -176,8 +178,31 @@ def test_tiled_apply_at_high_load_defers_exactly(fill):
         packed, offsets = to_device(rs)
         g.insert(packed, offsets)
         assert g.status() == dbg.OK
+        c = g.binned_counters()
+        assert c["binned"]
+        if mode == 2:  # long probe runs cross tile ends
+            assert c["deferred"] > 0
         assert_same_graph(g.export(), exp)
         g.close()
+
+
+def test_tile_bucket_overflow_goes_to_the_global_pass():
+    # one read repeated 1000 times: each of its keys brings 1000 events to its
+    # tile, well past the tile's bucket (the region's mean per tile, about
+    # 1500, plus the slack); the rest goes to the overflow area and the
+    # global pass applies it, still on the binned path
+    base = synth.ragged_reads(20000, 200, 21, 43)
+    rep = synth.codes_to_ascii(synth.random_genome(150, 44))
+    rs = synth.from_strings([base.read_ascii(r) for r in range(base.n_reads)] + [rep] * 1000, 21)
+    exp = oracle_export(rs)
+    g = binned_graph(rs, apply_mode=2)
+    packed, offsets = to_device(rs)
+    g.insert(packed, offsets)
+    assert g.status() == dbg.OK
+    c = g.binned_counters()
+    assert c["binned"] and c["overflow"] > 0, c
+    assert_same_graph(g.export(), exp)
+    g.close()
 
 
 def test_tiled_apply_respects_max_probes_with_a_spill():
@@ -212,4 +237,5 @@ def test_bucket_overflow_from_repeated_keys_falls_back_exactly():
     t = g.kernel_times()
     fallback = dbg.Graph.KERNELS.index("direct_fallback")
     assert t[-1, fallback] >= 0
+    assert not g.binned_counters()["binned"]
     g.close()

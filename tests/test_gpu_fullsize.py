@@ -44,6 +44,9 @@ def test_full_size_workload_matches_oracle_digests(name):
     g.insert(packed, offsets)
     del packed, offsets
     assert g.status() == dbg.OK
+    if g.info()["table_bytes"] >= 256 << 20:  # binned path: it did the work, no fall-back
+        c = g.binned_counters()
+        assert c["binned"] and c["overflow"] + c["deferred"] < rs.n_edges() // 100, c
     assert g.stats() == (gold["n_vertices"], gold["n_edges"])
     keys, counts = g.export()
     g.close()
