@@ -11,7 +11,8 @@
 //      sub-tiles; a single read wider than the window reads its bases from
 //      global memory);
 //   3. maps each thread to a run of R consecutive vertex positions of the
-//      flattened (sub-)tile; the first key of a run (or of a read inside it)
+//      flattened (sub-)tile (inside a window with 32-bit indices relative to
+//      the sub-tile and the window); the first key of a run (or of a read inside it)
 //      is extracted -- the k-1 bases, first base most significant -- from two
 //      64-bit window words with a funnel shift and a 2-bit-group reversal,
 //      and the next ones roll: key' = ((key << 2) | label) & mask, where the
@@ -32,9 +33,11 @@ constexpr int kWinWords = 2048;  // 16 KB window of packed bases per CTA (64 Ki 
 constexpr unsigned kFull = 0xffffffffu;
 
 // Dynamic shared memory the tile machinery uses (the visitor's own region
-// follows it, 16-byte aligned).
+// follows it, 16-byte aligned): the window, the reads' offsets and vertex
+// prefix (64-bit), and both again relative to the window (32-bit).
 __host__ __device__ constexpr size_t tile_smem_bytes(int tile_reads) {
-  return (size_t)(kWinWords + 2) * 8 + (size_t)(tile_reads + 1) * 16;
+  return (size_t)(kWinWords + 2) * 8 + (size_t)(tile_reads + 1) * 16 +
+         (((size_t)(tile_reads + 1) * 8 + 15) & ~(size_t)15);
 }
 
 // What a visitor learns about the item a vertex belongs to.
@@ -109,6 +112,10 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
   uint64_t *s_win = reinterpret_cast<uint64_t *>(smem_raw);  // kWinWords + 2
   uint64_t *s_off = s_win + kWinWords + 2;                     // tile_reads + 1
   uint64_t *s_vpre = s_off + tile_reads + 1;                   // tile_reads + 1
+  // inside a window: vertex prefix relative to the sub-tile's first vertex,
+  // read starts relative to the window's first base (tile_reads + 1 each)
+  uint32_t *s_vrel = reinterpret_cast<uint32_t *>(s_vpre + tile_reads + 1);
+  uint32_t *s_prel = s_vrel + tile_reads + 1;
 
   __shared__ ItemDesc s_item;
   __shared__ int s_item_idx;
@@ -232,12 +239,62 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
               done = nvec << 4;
             }
             for (uint64_t i = done + tid; i < nb; i += BLOCK) wbytes[i] = __ldg(packed + wb0 + i);
+            // the sub-tile's reads fit the window: 32-bit indices from here on
+            for (int i = ra + tid; i <= rb; i += BLOCK) {
+              s_vrel[i] = (uint32_t)(s_vpre[i] - s_vpre[ra]);
+              s_prel[i] = (uint32_t)(s_off[i] - origin - (wb0 << 2));
+            }
             __syncthreads();
           }
           const uint64_t v_lo = s_vpre[ra], v_hi = s_vpre[rb];
           const uint64_t mask = (1ull << (2 * m)) - 1ull;
-          const uint64_t wbase = wb0 << 2;  // base position of the window's first word
           int r = ra;
+          if (!gmode) {
+            // v: vertex index relative to v_lo; q: base position relative to
+            // the window; the read holding v spans vertices [., vr1) and
+            // bases [., qend)
+            const uint32_t nv = (uint32_t)(v_hi - v_lo);
+            for (uint32_t base = 0; base < nv; base += (uint32_t)BLOCK * R) {
+              if (!Visitor::kUniformRounds && vis.stop(lane)) break;
+              uint32_t v = base + (uint32_t)tid * R;
+              uint64_t key = kEmpty;
+              uint32_t label = 0, vr1 = 0, q = 0, qend = 0;
+              bool have = false;
+#pragma unroll
+              for (int sub = 0; sub < R; ++sub, ++v) {
+                const bool valid = v < nv;
+                bool edge = false;
+                if (valid) {
+                  bool fresh = !have;
+                  if (fresh || v >= vr1) {
+                    while (s_vrel[r + 1] <= v) ++r;
+                    vr1 = s_vrel[r + 1];
+                    q = s_prel[r] + (v - s_vrel[r]);
+                    qend = s_prel[r + 1];
+                    fresh = true;
+                  } else {
+                    ++q;
+                  }
+                  edge = q + (uint32_t)k <= qend;
+                  if (fresh) {
+                    const uint32_t wi = q >> 5;
+                    key = key_from_words(s_win[wi], s_win[wi + 1], (q & 31) * 2, m);
+                  } else {
+                    key = ((key << 2) | label) & mask;
+                  }
+                  const uint32_t qe = q + (uint32_t)m;
+                  label = (uint32_t)(s_win[qe >> 5] >> ((qe & 31) * 2)) & 3u;
+                  have = true;
+                }
+                vis.vertex(valid, key, edge, label, lane, sub, ctx);
+              }
+              if (Visitor::kUniformRounds) vis.round_end();
+            }
+            __syncthreads();
+            ra = rb;
+            continue;
+          }
+          // a read wider than the window: its bases come from global memory
           for (uint64_t base = v_lo; base < v_hi; base += (uint64_t)BLOCK * R) {
             if (!Visitor::kUniformRounds && vis.stop(lane)) break;
             uint64_t v = base + (uint64_t)tid * R;
@@ -262,23 +319,11 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
                   ++p;
                 }
                 edge = p + (uint64_t)k <= pend;
-                if (!gmode) {
-                  const uint64_t q = p - wbase;
-                  if (fresh) {
-                    const uint32_t wi = (uint32_t)(q >> 5);
-                    key = key_from_words(s_win[wi], s_win[wi + 1], (uint32_t)(q & 31) * 2, m);
-                  } else {
-                    key = ((key << 2) | label) & mask;
-                  }
-                  const uint32_t qe = (uint32_t)q + (uint32_t)m;
-                  label = (uint32_t)(s_win[qe >> 5] >> ((qe & 31) * 2)) & 3u;
+                if (fresh) {
+                  key = key_from_global(packed, nbytes, p, m, label);
                 } else {
-                  if (fresh) {
-                    key = key_from_global(packed, nbytes, p, m, label);
-                  } else {
-                    key = ((key << 2) | label) & mask;
-                    label = base_from_global(packed, nbytes, p + (uint64_t)m);
-                  }
+                  key = ((key << 2) | label) & mask;
+                  label = base_from_global(packed, nbytes, p + (uint64_t)m);
                 }
                 have = true;
               }
