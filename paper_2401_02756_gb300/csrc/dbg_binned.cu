@@ -7,19 +7,22 @@
 // random-sector rate of HBM.  So for a large table the insert runs as:
 //   buckets -- the read set's vertex positions, and for every table region
 //              (2^shift slots, at most 2048 regions) a bucket of its
-//              expected events plus six standard deviations;
+//              expected events plus a margin of several standard deviations;
 //   scatter -- walk the read tiles, compute every vertex's key and home
 //              slot, and write one 8-byte event per vertex,
 //              (key << 3) | (edge << 2) | label, into its region's bucket
 //              (block-local counting sort in shared memory; each flush's
 //              run appended to its bucket with one atomic);
-//   split   -- per region, order the events by 2048-slot table tile
-//              (units of events: histogram, offsets, counting-sorted scatter);
+//   split   -- per region, regroup the events into per-tile buckets of the
+//              region's mean per 2048-slot tile plus a margin (a counting
+//              sort per chunk in shared memory, one atomic per tile and
+//              chunk; what does not fit goes to an overflow area);
 //   apply   -- one CTA per tile: a bulk copy brings the tile into shared
 //              memory, the tile's events are applied there with
 //              shared-memory CAS and add, a bulk copy writes it back;
-//   deferred -- the few events whose probe left their tile, from their home
-//              slot, with the global find-or-claim.
+//   deferred -- the events whose probe left their tile and those of the
+//              overflow area, from their home slot, with the global
+//              find-or-claim.
 // The earlier streaming apply (all CTAs sweep the region-ordered events with
 // global atomics inside an L2-resident window) remains as apply_mode = 1; it
 // needs gap-free region ranges, so it keeps an exact count pass (histogram
