@@ -86,10 +86,15 @@ def measured_peaks():
 
 
 def kernel_source_digest():
+    """Digest of the insert kernels' code: their sources without line
+    comments and blank lines (a comment edit keeps recorded profiles valid)."""
     h = hashlib.sha256()
     for f in ("dbg_insert.cu", "dbg_binned.cu", "dbg_binned.cuh", "dbg_tiles.cuh", "dbg_internal.cuh",
               "dbg_tma.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2401_02756_gb300", "csrc", f), "rb").read())
+        for line in open(os.path.join(ROOT, "paper_2401_02756_gb300", "csrc", f), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
