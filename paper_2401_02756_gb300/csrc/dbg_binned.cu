@@ -952,35 +952,72 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threa
   }
 }
 
+// Slot fingerprints of the tile in shared memory: one byte per slot, 0 for an
+// empty slot, else the low byte of the key's hash (1..255; the home slot
+// comes from the high bits).  A probe step reads four slots' bytes at once
+// and looks for the event's byte or 0 with two zero-byte tests; only such a
+// candidate's key is read.  A warp then runs as long as its longest probe in
+// steps of four slots instead of one.
+constexpr int kFpBytes = kTileSlots + 16;  // (the last step reads one word past the tile)
+
+__device__ __forceinline__ uint32_t slot_fp(uint64_t h) {
+  const uint32_t f = (uint32_t)h & 0xFFu;
+  return f ? f : 1u;
+}
+
+// 0x80 in every byte of x that is zero, and possibly in bytes above a zero
+// byte (a borrow), never below the lowest zero byte.
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
+  return (x - 0x01010101u) & ~x & 0x80808080u;
+}
+
 // One event against the tile in shared memory: found or claimed and counted,
 // failed (max_probes inside the tile), or deferred (the probe left the tile).
-__device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint64_t first, int len,
-                                           uint64_t n_slots, uint32_t max_probes,
+// Slots are examined in probe order exactly as one at a time would: the first
+// slot from home that holds the key or is empty decides.
+__device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, uint64_t first,
+                                           int len, uint64_t n_slots, uint32_t max_probes,
                                            uint32_t *status, SpillRecord *spill,
                                            uint64_t spill_cap, unsigned long long *spill_count,
                                            uint64_t *deferred_ev, unsigned long long *deferred) {
   const unsigned long long key = e >> 3;
-  int q = (int)(home_slot(key, n_slots) - first);
-  uint32_t probes = 0;
-  while (q < len) {
-    const unsigned long long cur = st[q].key;
-    bool found = cur == key;
-    if (!found && cur == kEmpty) {
-      const unsigned long long prev = atomicCAS(&st[q].key, kEmpty, key);
+  const uint64_t h = fmix64(key);
+  const int home = (int)(__umul64hi(h, n_slots) - first);  // = home_slot(key) - first
+  const uint32_t f = slot_fp(h), f4 = f * 0x01010101u;
+  // the key can only sit in [home, limit): max_probes slots, or up to the tile's end
+  const bool capped = max_probes <= (uint32_t)(len - home);
+  const int limit = capped ? home + (int)max_probes : len;
+  const uint32_t *fp32 = reinterpret_cast<const uint32_t *>(fp);
+  int q = home;
+  while (q < limit) {
+    const uint32_t w = __funnelshift_r(fp32[q >> 2], fp32[(q >> 2) + 1], 8 * (q & 3));
+    uint32_t cand = zero_bytes(w ^ f4) | zero_bytes(w);
+    if (limit - q < 4) cand &= (1u << (8 * (limit - q))) - 1u;
+    if (cand == 0u) {
+      q += 4;
+      continue;
+    }
+    const int i = (__ffs(cand) >> 3) - 1;  // the first candidate's byte
+    const int sl = q + i;
+    bool found;
+    if (((w >> (8 * i)) & 0xFFu) == 0u) {  // empty (as far as the byte knows): claim it
+      const unsigned long long prev = atomicCAS(&st[sl].key, kEmpty, key);
+      if (prev == kEmpty) fp[sl] = (uint8_t)f;
       found = prev == kEmpty || prev == key;
+    } else {
+      found = st[sl].key == key;
     }
     if (found) {
-      if (e & 4ull) atomicAdd(&st[q].cnt[e & 3ull], 1u);
+      if (e & 4ull) atomicAdd(&st[sl].cnt[e & 3ull], 1u);
       return;
     }
-    if (++probes >= max_probes) {
-      spill_or_fail(spill, spill_cap, spill_count, status, key, (e & 4ull) != 0,
-                    (uint32_t)(e & 3ull));
-      return;
-    }
-    ++q;
+    q = sl + 1;  // another key (claimed meanwhile, or a byte collision): on to the next
   }
-  deferred_ev[atomicAdd(deferred, 1ull)] = e;  // left the tile: later, globally
+  if (capped)  // max_probes slots inside the tile: as the direct insert
+    spill_or_fail(spill, spill_cap, spill_count, status, key, (e & 4ull) != 0,
+                  (uint32_t)(e & 3ull));
+  else
+    deferred_ev[atomicAdd(deferred, 1ull)] = e;  // left the tile: later, globally
 }
 
 // Persistent CTAs take tiles: a bulk copy brings the tile into shared memory
@@ -994,7 +1031,8 @@ __global__ void __launch_bounds__(BLOCK)
                  unsigned long long *spill_count, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  Slot *st = reinterpret_cast<Slot *>(smem);  // kTileSlots slots
+  Slot *st = reinterpret_cast<Slot *>(smem);                 // kTileSlots slots
+  uint8_t *fp = smem + (size_t)kTileSlots * sizeof(Slot);   // kFpBytes fingerprints
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_stop, s_failed;
   if (threadIdx.x == 0) {
@@ -1024,8 +1062,22 @@ __global__ void __launch_bounds__(BLOCK)
     }
     uint64_t e[kBatch];
     load_batch<BLOCK>(ev2, a, b, e);  // overlaps the tile's arrival
-    if (!mbar_wait(&s_bar, parity)) atomicExch(&s_failed, 1u);
+    const bool landed = mbar_wait(&s_bar, parity);
+    if (!landed) atomicExch(&s_failed, 1u);
     parity ^= 1u;
+    if (landed) {  // the tile's fingerprints, four slots per word
+      uint32_t *fp32 = reinterpret_cast<uint32_t *>(fp);
+      for (int wi = threadIdx.x; wi < kFpBytes / 4; wi += BLOCK) {
+        uint32_t v = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int sl = 4 * wi + j;
+          const unsigned long long k = sl < len ? st[sl].key : kEmpty;
+          if (k != kEmpty) v |= slot_fp(fmix64(k)) << (8 * j);
+        }
+        fp32[wi] = v;
+      }
+    }
     __syncthreads();
     if (s_failed) {
       if (threadIdx.x == 0) {
@@ -1040,7 +1092,7 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
         for (int r = 0; r < kBatch; ++r)
           if (e[r] != kEmpty)
-            tile_event(e[r], st, first, len, n_slots, max_probes, status, spill, spill_cap,
+            tile_event(e[r], st, fp, first, len, n_slots, max_probes, status, spill, spill_cap,
                        spill_count, deferred_ev, aux.deferred);
         base += (uint64_t)BLOCK * kBatch;
         if (base >= b) break;
@@ -1372,10 +1424,11 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     }
     timer_mark(h, call, 5, s);
     {
-      // 512 threads: three such CTAs (64 KB of shared memory each) fill an SM
-      // with 48 warps, enough to hide the dependent hash and probe latencies
+      // 512 threads: three such CTAs (66 KB of shared memory each: the tile
+      // and its fingerprints) fill an SM with 48 warps, enough to hide the
+      // dependent hash and probe latencies
       constexpr int BA = 512;
-      constexpr size_t smem = (size_t)kTileSlots * sizeof(Slot);
+      constexpr size_t smem = (size_t)kTileSlots * sizeof(Slot) + kFpBytes;
       DBG_CK(cudaFuncSetAttribute(k_tile_apply<BA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
       int per_sm = 0;
