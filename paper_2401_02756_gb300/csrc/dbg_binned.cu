@@ -237,6 +237,32 @@ __global__ void __launch_bounds__(1024)
 // sort), and they are written out as runs.  A run's position = the slice's
 // run start in the region (reserved at the start of the slice, as long as
 // the count pass measured) + the events of the region already placed.
+// Exclusive prefix of `local` over a CTA of BLOCK threads with one barrier:
+// every warp scans the per-warp totals itself (no second pass by one warp).
+// `total` receives the CTA's sum.  s_w (BLOCK / 32 words) must not be
+// written again before the caller's next barrier.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t cta_exclusive_prefix(uint32_t local, uint32_t *s_w,
+                                                         uint32_t &total) {
+  static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "whole warps, at most 32 of them");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  uint32_t w = lane < BLOCK / 32 ? s_w[lane] : 0u;
+  for (int d = 1; d < BLOCK / 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(kFull, w, d);
+    if (lane >= d) w += o;
+  }
+  total = __shfl_sync(kFull, w, BLOCK / 32 - 1);
+  const uint32_t before = __shfl_sync(kFull, w, (warp + 31) & 31);  // warp - 1's inclusive sum
+  return incl - local + (warp > 0 ? before : 0u);
+}
+
 template <int BLOCK>
 struct ScatterVisitor {
   static constexpr bool kUniformRounds = true;
@@ -270,33 +296,16 @@ struct ScatterVisitor {
     }
   }
   __device__ void round_end() {
-    __shared__ unsigned long long s_w[BLOCK / 32];
-    __shared__ uint32_t s_total;
+    __shared__ uint32_t s_w[BLOCK / 32];
     __syncthreads();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     // exclusive prefix over the regions; each region's place in the output
     const int per = (parts + BLOCK - 1) / BLOCK;
     const int p0 = min(parts, tid * per), p1 = min(parts, p0 + per);
     uint32_t local = 0;
     for (int p = p0; p < p1; ++p) local += hist[p];
-    uint32_t incl = local;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += o;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned long long w = lane < BLOCK / 32 ? s_w[lane] : 0;
-      for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long o = __shfl_up_sync(kFull, w, d);
-        if (lane >= d) w += o;
-      }
-      if (lane < BLOCK / 32) s_w[lane] = w;
-      if (lane == BLOCK / 32 - 1) s_total = (uint32_t)w;
-    }
-    __syncthreads();
-    uint32_t run = incl - local + (warp > 0 ? (uint32_t)s_w[warp - 1] : 0u);
+    uint32_t total;
+    uint32_t run = cta_exclusive_prefix<BLOCK>(local, s_w, total);
     for (int p = p0; p < p1; ++p) {
       const uint32_t h = hist[p];
       off[p] = run;
@@ -328,14 +337,13 @@ struct ScatterVisitor {
       }
     }
     __syncthreads();
-    const uint32_t total = s_total;
     for (uint32_t j = tid; j < total; j += BLOCK) {
       const unsigned long long g = gbase[spid[j]];
       const unsigned long long at = g + j;
       if (g != ~0ull && at < cap) __stcs(out + at, sorted[j]);
     }
     // no barrier here: the next round only touches hist (already cleared)
-    // before its first barrier, and sorted / spid / gbase / s_total after it
+    // before its first barrier, and sorted / spid / gbase / s_w after it
   }
 };
 
@@ -805,7 +813,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threa
   __shared__ uint32_t s_warp[BLOCK / 32];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_failed;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int per = (tpr + BLOCK - 1) / BLOCK;  // bins per thread in the prefix
   const int j0 = min(tpr, tid * per), j1 = min(tpr, j0 + per);
   const uint64_t over_base = aux.region_base[parts];
@@ -884,23 +892,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threa
     // exclusive prefix of the chunk's tile counts
     uint32_t local = 0;
     for (int j = j0; j < j1; ++j) local += s_hist[j];
-    uint32_t incl = local;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += o;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = lane < BLOCK / 32 ? s_warp[lane] : 0u;
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(kFull, w, d);
-        if (lane >= d) w += o;
-      }
-      if (lane < BLOCK / 32) s_warp[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = incl - local + (warp > 0 ? s_warp[warp - 1] : 0u);
+    uint32_t chunk_total;
+    uint32_t run = cta_exclusive_prefix<BLOCK>(local, s_warp, chunk_total);
 #pragma unroll
     for (int q = 0; q < kMaxBinsPerThread; ++q) {
       const int j = j0 + q;
@@ -1030,7 +1023,7 @@ __global__ void __launch_bounds__(BLOCK)
                  uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
                  unsigned long long *spill_count, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];  // (bulk copies need 16 bytes)
   Slot *st = reinterpret_cast<Slot *>(smem);                 // kTileSlots slots
   uint8_t *fp = smem + (size_t)kTileSlots * sizeof(Slot);   // kFpBytes fingerprints
   __shared__ __align__(8) uint64_t s_bar;
