@@ -112,13 +112,16 @@ def test_auto_path_picks_binned_for_large_tables():
     rs = synth.ragged_reads(1000, 150, 21, 38)
     g = dbg.Graph(rs.k, (256 << 20) // 32)  # exactly the automatic threshold
     packed, offsets = to_device(rs)
+    assert g.binned_counters() == {"binned": False, "deferred": 0, "overflow": 0}  # no call yet
     g.insert(packed, offsets)
     assert g.info()["event_capacity"] > 0
+    assert g.binned_counters()["binned"]
     assert_same_graph(g.export(), oracle_export(rs))
     g.close()
     small = dbg.Graph(rs.k, capacity_for(rs))
     small.insert(packed, offsets)
     assert small.info()["event_capacity"] == 0
+    assert not small.binned_counters()["binned"]  # the direct path: no binned call
     small.close()
 
 
