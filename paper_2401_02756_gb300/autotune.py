@@ -23,8 +23,8 @@ def candidates(k: int, binned: bool) -> list[dict]:
     out = [dict(insert_path=1, block_threads=b, tile_reads=tr, warp_aggregate=a)
            for b, tr, a in itertools.product((128, 256), (64, 0), (0, 1))]
     if binned and k <= 31:
-        # the tiled apply over region sizes (0: its default of 2^20 slots)
-        out += [dict(insert_path=2, apply_mode=2, region_log2=r) for r in (0, 19, 21)]
+        # the tiled apply over region sizes (0: its default of 2^21 slots)
+        out += [dict(insert_path=2, apply_mode=2, region_log2=r) for r in (0, 20, 22)]
         # the streaming apply's launch shapes
         out += [dict(insert_path=2, apply_mode=1, apply_unroll=u, apply_chunk=m, apply_ctas=c,
                      region_log2=r)

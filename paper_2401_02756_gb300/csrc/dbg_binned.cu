@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(BLOCK)
 constexpr int kTileLog2 = 11;
 constexpr int kTileSlots = 1 << kTileLog2;  // 2048 slots = 64 KB of shared memory
 constexpr int kMaxTilesPerRegion = 4096;    // beyond this the streaming apply is used
-constexpr int kTiledShift = 20;             // automatic regions of the tiled path: 512 tiles
+constexpr int kTiledShift = 21;             // automatic regions of the tiled path: 1024 tiles
 
 constexpr int kBatch = 8;  // events each thread loads before it uses them (memory parallelism)
 
@@ -1327,7 +1327,8 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   const int tile_reads = std::min(t.tile_reads, B);
   // the tiled apply re-partitions each region by tile, so its first pass can
   // use coarser regions (fewer of them: a cheaper scatter); measured best at
-  // 512 tiles per region on the 100 Mbp workload
+  // 1024 tiles per region on the 100 Mbp workload (512: 50.1 ms, 1024: 49.5 ms,
+  // 256: 53.3 ms)
   const bool want_tiled = t.apply_mode != 1 && h->bin_cap < (1ull << 32);
   const BinGeometry geo =
       bin_geometry(h->n_slots, t.region_log2 > 0 ? t.region_log2 : (want_tiled ? kTiledShift : 0));
@@ -1410,7 +1411,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     // so that each tile's run in a chunk stays several events long
     if (tpr <= 256) {
       DBG_TRY((launch_tile_scatter<256, true>(h, mv, aux, geo, unit, tpr, sms, s)));
-    } else if (tpr <= 512) {
+    } else if (tpr <= 1024) {  // (1024 tiles: two bins per thread; measured faster than 1024 threads)
       DBG_TRY((launch_tile_scatter<512, true>(h, mv, aux, geo, unit, tpr, sms, s)));
     } else {
       DBG_TRY((launch_tile_scatter<1024, false>(h, mv, aux, geo, unit, tpr, sms, s)));
