@@ -974,7 +974,7 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, ui
                                            uint64_t spill_cap, unsigned long long *spill_count,
                                            uint64_t *deferred_ev, unsigned long long *deferred) {
   const unsigned long long key = e >> 3;
-  const uint64_t h = fmix64(key);
+  const uint64_t h = key_hash(key);
   const int home = (int)(__umul64hi(h, n_slots) - first);  // = home_slot(key) - first
   const uint32_t f = slot_fp(h), f4 = f * 0x01010101u;
   // the key can only sit in [home, limit): max_probes slots, or up to the tile's end
@@ -1066,7 +1066,7 @@ __global__ void __launch_bounds__(BLOCK)
         for (int j = 0; j < 4; ++j) {
           const int sl = 4 * wi + j;
           const unsigned long long k = sl < len ? st[sl].key : kEmpty;
-          if (k != kEmpty) v |= slot_fp(fmix64(k)) << (8 * j);
+          if (k != kEmpty) v |= slot_fp(key_hash(k)) << (8 * j);
         }
         fp32[wi] = v;
       }

@@ -80,8 +80,17 @@ __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t x) {
   return x;
 }
 
+// The table's key hash: a multiplication by 2^64 / golden ratio (Knuth's
+// multiplicative hashing) whose high bits choose the home slot, with the high
+// half folded into the low one so that the low byte is mixed too (the tiled
+// apply's slot fingerprints).
+__host__ __device__ __forceinline__ uint64_t key_hash(uint64_t key) {
+  const uint64_t x = key * 0x9E3779B97F4A7C15ull;
+  return x ^ (x >> 32);
+}
+
 __device__ __forceinline__ uint64_t home_slot(uint64_t key, uint64_t n_slots) {
-  return __umul64hi(fmix64(key), n_slots);
+  return __umul64hi(key_hash(key), n_slots);
 }
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
