@@ -507,7 +507,9 @@ def run_reference(args):
     oracle.build()
     rs = synth.WORKLOADS[args.workload]()
     cores = host_cores()
-    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    # about 100 s of oracle work in all (measured steps run ~1.5x the
+    # calibration's estimate: a larger sample holds more distinct vertices)
+    per_step = max(2.0, min(15.0, 100.0 / max(1, args.steps + args.warmup)))
     # size one step's sample from a calibration run
     _, _, n, _ = time_oracle_sample(rs, per_step, cores)
     nb = int((int(rs.offsets[n]) + 3) // 4)
