@@ -347,6 +347,8 @@ struct ScatterVisitor {
   }
 };
 
+constexpr int kScatterTileReads = 416;  // reads per scatter tile without a count pass (<= 512)
+
 template <int BLOCK>
 constexpr size_t scatter_smem(int tile_reads, int parts) {
   return tile_smem_bytes(tile_reads) + (size_t)BLOCK * kRun * (8 + 2) +
@@ -1324,7 +1326,6 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
                   cudaStream_t s, int call) {
   constexpr int B = 256;
   const dbg_tuning t = resolve_tuning(tuning);
-  const int tile_reads = std::min(t.tile_reads, B);
   // the tiled apply re-partitions each region by tile, so its first pass can
   // use coarser regions (fewer of them: a cheaper scatter); measured best at
   // 1024 tiles per region on the 100 Mbp workload (512: 50.1 ms, 1024: 49.5 ms,
@@ -1332,13 +1333,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   const bool want_tiled = t.apply_mode != 1 && h->bin_cap < (1ull << 32);
   const BinGeometry geo =
       bin_geometry(h->n_slots, t.region_log2 > 0 ? t.region_log2 : (want_tiled ? kTiledShift : 0));
-  const uint64_t slices = std::min<uint64_t>(tiles, kBinSlices);
   const MetaView mv = meta_view(h);
-
-  ItemPack<1> pk{};
-  pk.n_items = 1;
-  pk.total_tiles = tiles;
-  pk.d[0] = it;
   const int sms = std::max(1, h->sm_count);
 
   // binned calls on one handle share its scratch: order them.  Inside a
@@ -1353,6 +1348,16 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   // 2^32 events)
   const bool tiled = want_tiled && geo.shift >= kTileLog2 && tpr <= kMaxTilesPerRegion &&
                      ensure_tile_scratch(h, geo, tpr, capturing);
+  // the read walk's own tiles ('tiles' counts the direct kernel's): the count
+  // pass and the scatter must walk the same ones; without a count pass the
+  // scatter takes larger tiles (fewer per-tile setups)
+  const int tile_reads = tiled ? kScatterTileReads : std::min(t.tile_reads, B);
+  const uint64_t walk_tiles = (it.n_reads + (uint64_t)tile_reads - 1) / (uint64_t)tile_reads;
+  const uint64_t slices = std::min<uint64_t>(walk_tiles, kBinSlices);
+  ItemPack<1> pk{};
+  pk.n_items = 1;
+  pk.total_tiles = walk_tiles;
+  pk.d[0] = it;
   DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, geo.parts * sizeof(unsigned long long), s));
   h->bin_counters = nullptr;

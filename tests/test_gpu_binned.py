@@ -158,6 +158,9 @@ def test_kernel_timer_records_the_kernels_each_path_launches():
     # the tiled apply over region sizes of 32 .. 4096 tiles (2^26: streaming fall-back)
     dict(apply_mode=2), dict(apply_mode=2, region_log2=16), dict(apply_mode=2, region_log2=20),
     dict(apply_mode=2, region_log2=23), dict(apply_mode=2, region_log2=26),
+    # the direct kernel's tiles (512 reads) differ from the binned walk's
+    dict(block_threads=512), dict(block_threads=512, apply_mode=1),
+    dict(block_threads=128, tile_reads=96),
 ])
 def test_binned_tuning_independence(tuning):
     rs = synth.ragged_reads(2500, 250, 27, 40, lead=1)
