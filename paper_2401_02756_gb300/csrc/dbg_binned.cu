@@ -230,13 +230,6 @@ __global__ void __launch_bounds__(1024)
 
 // --- K1d --------------------------------------------------------------------
 
-// A round of the tile walk gives every thread kRun events; each keeps them in
-// registers with its region and its rank in the region (a shared-memory
-// atomic), then the round is flushed: an exclusive prefix of the region
-// counts places the events in region order in shared memory (counting
-// sort), and they are written out as runs.  A run's position = the slice's
-// run start in the region (reserved at the start of the slice, as long as
-// the count pass measured) + the events of the region already placed.
 // Exclusive prefix of `local` over a CTA of BLOCK threads with one barrier:
 // every warp scans the per-warp totals itself (no second pass by one warp).
 // `total` receives the CTA's sum.  s_w (BLOCK / 32 words) must not be
@@ -263,6 +256,14 @@ __device__ __forceinline__ uint32_t cta_exclusive_prefix(uint32_t local, uint32_
   return incl - local + (warp > 0 ? before : 0u);
 }
 
+// A round of the tile walk gives every thread kRun events; each keeps them in
+// registers with its region and its rank in the region (a shared-memory
+// atomic), then the round is flushed: an exclusive prefix of the region
+// counts places the events in region order in shared memory (counting
+// sort), and they are written out as runs.  A run's position: without a
+// count pass (the tiled path), one atomic on the region's bucket cursor per
+// round; after a count pass, the slice's run start in the region (reserved
+// at the start of the slice) + the events of the region already placed.
 template <int BLOCK>
 struct ScatterVisitor {
   static constexpr bool kUniformRounds = true;
