@@ -214,6 +214,26 @@ int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offset
 int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
                           uint64_t n_reads, void *stream);
 
+/* Build the graph of n_reads reads from scratch: the table's previous
+ * contents are discarded (as dbg_reset) and every k-mer is inserted (as
+ * dbg_insert_reads), in one stream-ordered call on `stream`.  The result is
+ * the graph dbg_reset followed by dbg_insert_reads gives.  On the binned path
+ * (see dbg_insert_reads) the emptying costs no pass of its own: the tiled
+ * apply starts every table tile as EMPTY slots in shared memory instead of
+ * reading it, and writes every tile -- with events or without -- exactly
+ * once.  So the table is not valid until the stream has passed the call:
+ * no other call may use the handle from another stream meanwhile.  The
+ * sticky status and pending spill records are cleared first.  n_reads == 0
+ * only empties the table.  Errors: as dbg_insert_reads. */
+int dbg_build_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                    uint64_t n_reads, void *stream);
+
+/* dbg_build_reads with `packed` and `offsets` in HOST memory, staged as
+ * dbg_insert_reads_host stages them (the first chunk's insert does the
+ * emptying, later chunks add to it).  Errors: as dbg_insert_reads_host. */
+int dbg_build_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                         uint64_t n_reads, void *stream);
+
 /* One item of a batched insert: a target graph and its reads (device
  * pointers, same conventions as dbg_insert_reads). */
 typedef struct dbg_batch_item {
@@ -273,11 +293,13 @@ int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *strea
  * cudaMemcpyDefault); either may be NULL to skip it.  Waits for `stream`.
  * *n_out receives the number of vertices D.  If D > max_n nothing is
  * written and DBG_ERR_BUFFER_TOO_SMALL is returned (a call with max_n = 0
- * is therefore a size query).  Temporary device memory (about 48 bytes per
- * vertex, 80 for k > 32) comes from a stream-ordered pool the library keeps
- * per device (up to 1 GiB of it stays cached between calls) and is
- * released to it before return.  Errors: INVALID_ARG, OOM, CUDA, BUFFER_TOO_SMALL, and the sticky
- * status (nothing exported when it is set). */
+ * is therefore a size query).  Temporary device memory comes from a
+ * stream-ordered pool the library keeps per device (up to 4 GiB of it stays
+ * cached between calls) and is released to it before return: 4 bytes per
+ * vertex when both outputs are 16-byte aligned device buffers and k <= 32
+ * (the sort then runs inside keys_out and counts_out), otherwise about 40
+ * bytes per vertex (80 for k > 32).  Errors: INVALID_ARG, OOM, CUDA,
+ * BUFFER_TOO_SMALL, and the sticky status (nothing exported when it is set). */
 int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, uint64_t max_n,
                       uint64_t *n_out, void *stream);
 
@@ -336,6 +358,11 @@ int dbg_find_contigs(dbg_handle h, char *bases_out, uint64_t max_bases, uint64_t
  *   - every call on a device shares the one array: calls whose GPU work
  *     overlaps (different streams, or host threads) race and must be
  *     serialised by the caller.
+ *   - keys of one word only: a graph with k > 32 is refused with
+ *     DBG_ERR_INVALID_ARG (dbg_export_sorted exports those);
+ *   - the looked-up address is kept until the process exits: after a
+ *     cudaDeviceReset of that device it is stale, and the entry point must
+ *     not be used again in that process.
  * Waits for `stream`.  Errors: INVALID_ARG, CUDA, BUFFER_TOO_SMALL (max_n <
  * vertices), NOALLOC_LIMIT, and the sticky status. */
 int dbg_export_sorted_noalloc(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out,
@@ -426,6 +453,12 @@ const char *dbg_strerror(int code);
 
 /* Text of the last CUDA error seen by this library on this thread ("" if none). */
 const char *dbg_last_cuda_error(void);
+
+/* The architecture the library's kernels were compiled for, as the CUDA
+ * runtime reports it for the current device (cudaFuncGetAttributes'
+ * binaryVersion: major * 10 + minor, 103 for sm_103a).  Needs a GPU.
+ * Errors: INVALID_ARG (NULL), CUDA (no device, or no kernel image for it). */
+int dbg_binary_version(int *out);
 
 /* ------------------------------------------------------------------------ */
 /* Measurement kernels: the random-sector ceiling the insert is rated on.   */

@@ -1019,7 +1019,22 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, ui
 // Persistent CTAs take tiles: a bulk copy brings the tile into shared memory
 // while the threads load their first events; the events are applied there;
 // a bulk copy writes the tile back while the CTA moves to its next tile.
-template <int BLOCK>
+//
+// FRESH: the table is being rebuilt from empty (dbg_build_reads), so its
+// contents are not read at all: every tile starts in shared memory as EMPTY
+// slots with zero counters and fingerprints, and every tile of the table --
+// with events or without -- is written back.  That one write is the table's
+// reset: the separate emptying pass (a full write of the table) disappears.
+// Each thread copies out and then re-initialises the same 16-byte words of
+// the tile, so the next tile needs no extra barrier.
+__device__ __forceinline__ void empty_tile_words(uint4 *st4, uint32_t *fp32) {
+  const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);  // key EMPTY, cnt[0..1]
+  const uint4 tail = make_uint4(0u, 0u, 0u, 0u);                    // cnt[2..3], pad
+  for (int i = threadIdx.x; i < 2 * kTileSlots; i += blockDim.x) st4[i] = (i & 1) ? tail : head;
+  for (int i = threadIdx.x; i < kFpBytes / 4; i += blockDim.x) fp32[i] = 0u;
+}
+
+template <int BLOCK, bool FRESH>
 __global__ void __launch_bounds__(BLOCK)
     k_tile_apply(const uint64_t *__restrict__ ev2, uint64_t *deferred_ev, TileAux aux, int tpr,
                  uint64_t n_tiles, Slot *table, uint64_t n_slots, uint32_t max_probes,
@@ -1029,9 +1044,13 @@ __global__ void __launch_bounds__(BLOCK)
   extern __shared__ __align__(16) unsigned char smem[];  // (bulk copies need 16 bytes)
   Slot *st = reinterpret_cast<Slot *>(smem);                 // kTileSlots slots
   uint8_t *fp = smem + (size_t)kTileSlots * sizeof(Slot);   // kFpBytes fingerprints
+  uint4 *st4 = reinterpret_cast<uint4 *>(smem);
+  uint32_t *fp32 = reinterpret_cast<uint32_t *>(fp);
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_stop, s_failed;
-  if (threadIdx.x == 0) {
+  if constexpr (FRESH) {
+    empty_tile_words(st4, fp32);
+  } else if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
     s_failed = 0u;
@@ -1045,43 +1064,62 @@ __global__ void __launch_bounds__(BLOCK)
     const uint64_t a = aux.region_base[p] + (t - p * (uint64_t)tpr) * cap;
     const uint64_t b = a + min(aux.fill[t], cap);
     const uint64_t first = t << kTileLog2;
-    // no event, or a tile past the table's end (never has one): the tile stays
-    // as it is (the same decision for the whole CTA)
-    if (a == b || first >= n_slots) continue;
+    // a tile past the table's end (never has an event) is not there at all
+    if (first >= n_slots) continue;
     const int len = (int)min((uint64_t)kTileSlots, n_slots - first);
-    const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(Slot);
-    if (threadIdx.x == 0) {
-      s_stop = ld_volatile_u32(status);
-      bulk_wait_read_all();  // the previous tile's write-back has left `st`
-      mbar_expect_tx(&s_bar, bytes);
-      bulk_load(st, table + first, bytes, &s_bar);
-    }
     uint64_t e[kBatch];
-    load_batch<BLOCK>(ev2, a, b, e);  // overlaps the tile's arrival
-    const bool landed = mbar_wait(&s_bar, parity);
-    if (!landed) atomicExch(&s_failed, 1u);
-    parity ^= 1u;
-    if (landed) {  // the tile's fingerprints, four slots per word
-      uint32_t *fp32 = reinterpret_cast<uint32_t *>(fp);
-      for (int wi = threadIdx.x; wi < kFpBytes / 4; wi += BLOCK) {
-        uint32_t v = 0u;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int sl = 4 * wi + j;
-          const unsigned long long k = sl < len ? st[sl].key : kEmpty;
-          if (k != kEmpty) v |= slot_fp(key_hash(k)) << (8 * j);
-        }
-        fp32[wi] = v;
+    if constexpr (FRESH) {
+      uint4 *dst = reinterpret_cast<uint4 *>(table + first);
+      if (a == b) {  // no event: the tile is written as it starts, EMPTY
+        const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
+        const uint4 tail = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = threadIdx.x; i < 2 * len; i += BLOCK) __stcs(dst + i, (i & 1) ? tail : head);
+        continue;  // (shared memory untouched: still the EMPTY tile)
       }
-    }
-    __syncthreads();
-    if (s_failed) {
+      if (threadIdx.x == 0) s_stop = ld_volatile_u32(status);
+      load_batch<BLOCK>(ev2, a, b, e);
+      __syncthreads();  // s_stop; the tile's EMPTY words (the previous copy-out re-made them)
+    } else {
+      // no event: the tile stays as it is (the same decision for the whole CTA)
+      if (a == b) continue;
+      const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(Slot);
       if (threadIdx.x == 0) {
-        set_sticky(status, DBG_ERR_TIMEOUT);
-        mbar_wait(&s_bar, parity ^ 1u);  // give the copy one more bounded chance to land
-        bulk_wait_all();
+        s_stop = ld_volatile_u32(status);
+        bulk_wait_read_all();  // the previous tile's write-back has left `st`
+        mbar_expect_tx(&s_bar, bytes);
+        bulk_load(st, table + first, bytes, &s_bar);
       }
-      return;
+      load_batch<BLOCK>(ev2, a, b, e);  // overlaps the tile's arrival
+      const bool landed = mbar_wait(&s_bar, parity);
+      if (!landed) atomicExch(&s_failed, 1u);
+      parity ^= 1u;
+      if (landed) {  // the tile's fingerprints, four slots per word
+        for (int wi = threadIdx.x; wi < kFpBytes / 4; wi += BLOCK) {
+          uint32_t v = 0u;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int sl = 4 * wi + j;
+            const unsigned long long k = sl < len ? st[sl].key : kEmpty;
+            if (k != kEmpty) v |= slot_fp(key_hash(k)) << (8 * j);
+          }
+          fp32[wi] = v;
+        }
+      }
+      __syncthreads();
+      if (s_failed) {
+        // The copy did not land within the bound.  Before the CTA leaves, the
+        // copy must no longer target its shared memory: wait for the same
+        // phase again with the same bound (a bulk copy from valid memory
+        // lands, so a second bound is only a guard), and for the write-backs
+        // this thread issued.
+        if (threadIdx.x == 0) {
+          set_sticky(status, DBG_ERR_TIMEOUT);
+          mbar_wait(&s_bar, parity ^ 1u);
+          bulk_wait_all();
+        }
+        __syncthreads();
+        return;
+      }
     }
     if (s_stop == 0u) {  // an earlier error stops the insert, as in the direct kernel
       for (uint64_t base = a;;) {
@@ -1096,13 +1134,25 @@ __global__ void __launch_bounds__(BLOCK)
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && s_stop == 0u) {
+    if constexpr (FRESH) {
+      // copy the tile out (written even after an earlier error: the table is
+      // at least empty there) and re-make the EMPTY tile, word by word
+      uint4 *dst = reinterpret_cast<uint4 *>(table + first);
+      const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
+      const uint4 tail = make_uint4(0u, 0u, 0u, 0u);
+      for (int i = threadIdx.x; i < 2 * kTileSlots; i += BLOCK) {
+        if (i < 2 * len) __stcs(dst + i, st4[i]);
+        st4[i] = (i & 1) ? tail : head;
+      }
+      for (int i = threadIdx.x; i < kFpBytes / 4; i += BLOCK) fp32[i] = 0u;
+      // (the next tile's barrier orders these writes before its events)
+    } else if (threadIdx.x == 0 && s_stop == 0u) {
       fence_proxy_async_smem();  // the CTA's shared-memory updates, before the bulk read
-      bulk_store(table + first, st, bytes);
+      bulk_store(table + first, st, (uint32_t)len * (uint32_t)sizeof(Slot));
       bulk_commit();
     }
   }
-  if (threadIdx.x == 0) bulk_wait_all();
+  if (!FRESH && threadIdx.x == 0) bulk_wait_all();
 }
 
 // The events that left their tile, then those of the overflow area, from
@@ -1324,7 +1374,7 @@ int launch_tile_scatter(dbg_handle h, const MetaView &mv, const TileAux &aux,
 }
 
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
-                  cudaStream_t s, int call) {
+                  cudaStream_t s, int call, bool fresh) {
   constexpr int B = 256;
   const dbg_tuning t = resolve_tuning(tuning);
   // the tiled apply re-partitions each region by tile, so its first pass can
@@ -1359,6 +1409,9 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   pk.n_items = 1;
   pk.total_tiles = walk_tiles;
   pk.d[0] = it;
+  // a rebuild from empty folds the reset into the tiled apply; the other
+  // applies read the table, so it is emptied first
+  if (fresh && !tiled) DBG_TRY(launch_table_init(h->table, h->n_slots, s));
   DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, geo.parts * sizeof(unsigned long long), s));
   h->bin_counters = nullptr;
@@ -1429,14 +1482,14 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
       // dependent hash and probe latencies
       constexpr int BA = 512;
       constexpr size_t smem = (size_t)kTileSlots * sizeof(Slot) + kFpBytes;
-      DBG_CK(cudaFuncSetAttribute(k_tile_apply<BA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+      auto kern = fresh ? k_tile_apply<BA, true> : k_tile_apply<BA, false>;
+      DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
-      DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_apply<BA>, BA, smem));
+      DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BA, smem));
       const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)std::max(1, per_sm) * sms);
-      k_tile_apply<BA><<<(int)grid, BA, smem, s>>>(
-          h->bin_ev2, h->bin_ev, aux, tpr, n_tiles, h->table, h->n_slots, h->max_probes,
-          h->d_status, h->d_spill, h->spill_cap, h->d_spill_count, mv.flag);
+      kern<<<(int)grid, BA, smem, s>>>(h->bin_ev2, h->bin_ev, aux, tpr, n_tiles, h->table,
+                                       h->n_slots, h->max_probes, h->d_status, h->d_spill,
+                                       h->spill_cap, h->d_spill_count, mv.flag);
       DBG_CK(cudaGetLastError());
     }
     timer_mark(h, call, 6, s);
@@ -1452,8 +1505,10 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
       default: DBG_TRY(launch_apply_m<B, 4>(h, mv, geo, sms, t, s)); break;
     }
   }
-  // the direct insert runs only if the events did not fit the buffer
+  // the direct insert runs only if the events did not fit the buffer (then no
+  // binned kernel touched the table: a rebuild from empty empties it first)
   timer_mark(h, call, 7, s);
+  if (fresh && tiled) DBG_TRY(launch_table_init(h->table, h->n_slots, s, mv.flag));
   const int st = launch_insert(&it, 1, tiles, tuning, h->sm_count, s, mv.flag);
   if (st != DBG_OK) return st;
   timer_mark(h, call, 8, s);

@@ -39,8 +39,11 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events);
 // Insert one read set through count / scan / scatter / apply, falling back to
 // the direct kernel on the device when the events do not fit the buffer.
 // `call`: the kernel timer's ring slot for this call (-1: not timed).
+// `fresh`: the table is rebuilt from empty (its contents are discarded); the
+// tiled apply then writes every tile from an EMPTY tile in shared memory
+// instead of reading it, which empties the table without a pass of its own.
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
-                  cudaStream_t s, int call);
+                  cudaStream_t s, int call, bool fresh = false);
 
 // The last binned call's counters (synchronizes the device): out[0] = 1 if
 // the binned kernels did its work, out[1] = events whose probe left their

@@ -287,7 +287,10 @@ int launch_insert(const ItemDesc *items, int n_items, uint64_t total_tiles,
 dbg_tuning resolve_tuning(const dbg_tuning &t);
 
 // Table kernels.
-int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream);
+// (gate: if not null, the kernel does nothing when *gate != 0, read on the
+// device when it runs -- the binned path's "binned kernels did the work" flag)
+int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream,
+                      const uint32_t *gate = nullptr);
 int launch_stats(const Slot *table, uint64_t n_slots, unsigned long long *acc, cudaStream_t stream,
                  bool wide);
 // Graphs with k > 32 (128-bit keys, dbg_wide.cu).

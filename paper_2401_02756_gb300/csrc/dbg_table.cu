@@ -26,9 +26,11 @@ int cuda_fail(cudaError_t e, const char *what) {
 // pool per device, owned by the library, that keeps up to kScratchKeep
 // bytes across synchronisations (the default pool would give every byte
 // back at each one, so a loop of exports would map and unmap memory each
-// time).  Anything above that is released as usual.
+// time).  Anything above that is released as usual.  4 GiB covers the
+// export of a graph of about 900 million vertices into device buffers (4
+// bytes a vertex plus the sort's histograms).
 namespace {
-constexpr uint64_t kScratchKeep = 1ull << 30;
+constexpr uint64_t kScratchKeep = 4ull << 30;
 std::mutex g_pool_mu;
 cudaMemPool_t g_pools[64] = {};
 }  // namespace
@@ -74,7 +76,8 @@ struct DeviceGuard {
 };
 
 // K2: every slot EMPTY with zero counters; two 16-byte stores per slot.
-__global__ void k_table_init(uint4 *t, uint64_t n_vec) {
+__global__ void k_table_init(uint4 *t, uint64_t n_vec, const uint32_t *gate) {
+  if (gate != nullptr && ld_volatile_u32(gate) != 0u) return;
   const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
   const uint4 tail = make_uint4(0u, 0u, 0u, 0u);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -111,14 +114,15 @@ int stream_grid(int sm_count, int per_sm) { return std::max(1, sm_count) * per_s
 
 }  // namespace
 
-int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream) {
+int launch_table_init(Slot *table, uint64_t n_slots, cudaStream_t stream, const uint32_t *gate) {
   int dev = 0, sms = 0;
   DBG_CK(cudaGetDevice(&dev));
   DBG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const uint64_t n_vec = n_slots * 2;
   uint64_t want = (n_vec + 255) / 256;
   const int grid = (int)std::min<uint64_t>(want, (uint64_t)stream_grid(sms, 8));
-  k_table_init<<<std::max(grid, 1), 256, 0, stream>>>(reinterpret_cast<uint4 *>(table), n_vec);
+  k_table_init<<<std::max(grid, 1), 256, 0, stream>>>(reinterpret_cast<uint4 *>(table), n_vec,
+                                                      gate);
   DBG_CK(cudaGetLastError());
   return DBG_OK;
 }
@@ -496,16 +500,22 @@ bool want_binned(dbg_handle h) {
   return h->n_slots * sizeof(dbg::Slot) >= dbg::kBinMinTableBytes;
 }
 
-int insert_one(dbg_handle h, const dbg::ItemDesc &it, uint64_t tiles, cudaStream_t s) {
+// fresh: the table's contents are discarded first (dbg_build_reads); the
+// binned path folds that into its tiled apply, the others empty the table
+// with the init kernel before they insert.
+int insert_one(dbg_handle h, const dbg::ItemDesc &it, uint64_t tiles, cudaStream_t s,
+               bool fresh = false) {
   const int call = dbg::timer_begin_call(h);
+  const bool binned =
+      h->k <= 32 && want_binned(h) && (h->bin_cap > 0 || dbg::ensure_bin_scratch(h, 0) == DBG_OK);
+  if (binned) return dbg::launch_binned(h, it, tiles, h->tuning, s, call, fresh);
+  if (fresh) DBG_TRY(dbg::launch_table_init(h->table, h->n_slots, s));
   if (h->k > 32) {  // 128-bit keys: their own kernel
     dbg::timer_mark(h, call, 0, s);
     const int st = dbg::launch_insert_wide(it, h->sm_count, s);
     dbg::timer_mark(h, call, 1, s);
     return st;
   }
-  if (want_binned(h) && (h->bin_cap > 0 || dbg::ensure_bin_scratch(h, 0) == DBG_OK))
-    return dbg::launch_binned(h, it, tiles, h->tuning, s, call);
   dbg::timer_mark(h, call, 0, s);
   const int st = dbg::launch_insert(&it, 1, tiles, h->tuning, h->sm_count, s);
   dbg::timer_mark(h, call, 1, s);  // direct call: kernel 0 spans marks 0..1
@@ -529,6 +539,33 @@ extern "C" int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint6
   const uint64_t tiles = (n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
   const dbg::ItemDesc it = dbg::make_item(h, packed, offsets, n_reads, 0);
   return insert_one(h, it, tiles, static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+// The sticky status and the spill count back to zero, stream-ordered (the
+// part of dbg_reset that is not the table).
+int clear_status(dbg_handle h, cudaStream_t s) {
+  DBG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s));
+  DBG_CK(cudaMemsetAsync(h->d_spill_count, 0, sizeof(unsigned long long), s));
+  return DBG_OK;
+}
+
+}  // namespace
+
+extern "C" int dbg_build_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                               uint64_t n_reads, void *stream) {
+  if (!h) return DBG_ERR_INVALID_ARG;
+  if (n_reads > 0 && (!packed || !offsets)) return DBG_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DBG_TRY(clear_status(h, s));
+  if (n_reads == 0) return dbg::launch_table_init(h->table, h->n_slots, s);
+  const dbg_tuning t = dbg::resolve_tuning(h->tuning);
+  const uint64_t tiles = (n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
+  const dbg::ItemDesc it = dbg::make_item(h, packed, offsets, n_reads, 0);
+  return insert_one(h, it, tiles, s, /*fresh=*/true);
 }
 
 namespace {
@@ -595,15 +632,21 @@ static bool offsets_non_decreasing(const uint64_t *offsets, uint64_t n_reads) {
   return std::all_of(ok.begin(), ok.end(), [](char c) { return c != 0; });
 }
 
-extern "C" int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
-                                     uint64_t n_reads, void *stream) {
+// dbg_insert_reads_host, or with `fresh` dbg_build_reads_host: the first
+// chunk's insert then discards the table's contents (later chunks add to it).
+static int insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                             uint64_t n_reads, void *stream, bool fresh) {
   if (!h) return DBG_ERR_INVALID_ARG;
-  if (n_reads == 0) return DBG_OK;
-  if (!packed || !offsets) return DBG_ERR_INVALID_ARG;
-  if (!offsets_non_decreasing(offsets, n_reads)) return DBG_ERR_INVALID_ARG;
+  if (n_reads > 0 && (!packed || !offsets)) return DBG_ERR_INVALID_ARG;
+  if (n_reads > 0 && !offsets_non_decreasing(offsets, n_reads)) return DBG_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (fresh) {
+    DBG_TRY(clear_status(h, s));
+    if (n_reads == 0) return dbg::launch_table_init(h->table, h->n_slots, s);
+  }
+  if (n_reads == 0) return DBG_OK;
   const dbg_tuning t = dbg::resolve_tuning(h->tuning);
 
   // chunk boundaries: the whole input when it is small enough (one insert,
@@ -654,11 +697,21 @@ extern "C" int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const 
     const dbg::ItemDesc it =
         dbg::make_item(h, h->stage_packed[b], h->stage_offsets[b], r1 - r0, byte0 * 4);
     const uint64_t tiles = (r1 - r0 + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
-    st = insert_one(h, it, tiles, s);
+    st = insert_one(h, it, tiles, s, fresh && c == 0);
     if (st != DBG_OK) return st;
     DBG_CK(cudaEventRecord(h->ev_consumed[b], s));
   }
   return DBG_OK;
+}
+
+extern "C" int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                                     uint64_t n_reads, void *stream) {
+  return insert_reads_host(h, packed, offsets, n_reads, stream, false);
+}
+
+extern "C" int dbg_build_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
+                                    uint64_t n_reads, void *stream) {
+  return insert_reads_host(h, packed, offsets, n_reads, stream, true);
 }
 
 extern "C" int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *stream) {
@@ -785,3 +838,12 @@ extern "C" const char *dbg_strerror(int code) {
 }
 
 extern "C" const char *dbg_last_cuda_error(void) { return dbg::g_last_error; }
+
+extern "C" int dbg_binary_version(int *out) {
+  if (!out) return DBG_ERR_INVALID_ARG;
+  *out = 0;
+  cudaFuncAttributes a{};
+  DBG_CK(cudaFuncGetAttributes(&a, dbg::k_table_init));
+  *out = a.binaryVersion;
+  return DBG_OK;
+}

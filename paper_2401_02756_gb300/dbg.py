@@ -30,12 +30,13 @@ EXPORTED = [
     "dbg_reserve_events", "dbg_enable_kernel_timing", "dbg_kernel_times", "dbg_binned_counters",
     "dbg_set_spill",
     "dbg_grow",
-    "dbg_insert_reads", "dbg_insert_reads_host", "dbg_insert_batch", "dbg_get_status", "dbg_stats",
+    "dbg_insert_reads", "dbg_insert_reads_host", "dbg_build_reads", "dbg_build_reads_host",
+    "dbg_insert_batch", "dbg_get_status", "dbg_stats",
     "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_normalize", "dbg_find_contigs", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
     "dbg_probe_random_sectors", "dbg_probe_window", "dbg_sketch_reads", "dbg_sketch_batch",
     "dbg_sketch_estimate",
     "dbg_mlp_work_floats", "dbg_mlp_features", "dbg_mlp_init", "dbg_mlp_forward",
-    "dbg_mlp_train_step",
+    "dbg_mlp_train_step", "dbg_binary_version",
 ]
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 1024, 64, 69825
 SKETCH_REGISTERS = 1024
@@ -105,6 +106,8 @@ def load() -> ctypes.CDLL:
         "dbg_binned_counters": (I, [P, ctypes.POINTER(U64)]),
         "dbg_insert_reads": (I, [P, P, P, U64, P]),
         "dbg_insert_reads_host": (I, [P, P, P, U64, P]),
+        "dbg_build_reads": (I, [P, P, P, U64, P]),
+        "dbg_build_reads_host": (I, [P, P, P, U64, P]),
         "dbg_insert_batch": (I, [ctypes.POINTER(BatchItem), I, P]),
         "dbg_get_status": (I, [P, P]),
         "dbg_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
@@ -115,6 +118,7 @@ def load() -> ctypes.CDLL:
         "dbg_pack_ascii": (I, [ctypes.c_char_p, U64, P, I, ctypes.POINTER(U64)]),
         "dbg_strerror": (ctypes.c_char_p, [I]),
         "dbg_last_cuda_error": (ctypes.c_char_p, []),
+        "dbg_binary_version": (I, [ctypes.POINTER(I)]),
         "dbg_probe_random_sectors": (I, [P, U64, U64, U64, I, P]),
         "dbg_probe_window": (I, [P, U64, U64, U64, U64, I, P]),
         "dbg_sketch_reads": (I, [I, P, P, U64, P, P]),
@@ -321,6 +325,22 @@ class Graph:
                                             int(of.size) - 1, _stream(stream)),
                "dbg_insert_reads_host")
 
+    def build(self, packed, offsets, n_reads: int | None = None, stream=None) -> None:
+        """Discard the graph and build it from reads in device memory (one
+        stream-ordered call: dbg_reset + dbg_insert_reads)."""
+        if n_reads is None:
+            n_reads = int(offsets.numel()) - 1
+        _check(load().dbg_build_reads(self.handle, _dptr(packed) or None, _dptr(offsets) or None,
+                                      int(n_reads), _stream(stream)), "dbg_build_reads")
+
+    def build_host(self, packed, offsets, stream=None) -> None:
+        """dbg_build_reads with reads in host memory."""
+        pk = _host_view(packed, np.uint8)
+        of = _host_view(offsets, np.uint64)
+        _check(load().dbg_build_reads_host(self.handle, _hptr(pk) or None, _hptr(of) or None,
+                                           int(of.size) - 1, _stream(stream)),
+               "dbg_build_reads_host")
+
     # -- results ------------------------------------------------------------
     def status(self, stream=None) -> int:
         return int(load().dbg_get_status(self.handle, _stream(stream)))
@@ -381,6 +401,16 @@ class Graph:
                "dbg_find_contigs")
         raw = bases.tobytes().decode("ascii")
         return [raw[int(offs[i]):int(offs[i + 1])] for i in range(n.value)]
+
+    def export_into(self, keys, counts, stream=None) -> int:
+        """One dbg_export_sorted call into caller-owned CUDA tensors (keys
+        int64 [>= D] or [>= D, 2], counts int32 [>= D, 4]); returns D.  Raises
+        if they hold fewer than D rows."""
+        n = ctypes.c_uint64()
+        rows = min(int(keys.shape[0]), int(counts.shape[0]))
+        _check(load().dbg_export_sorted(self.handle, keys.data_ptr(), counts.data_ptr(), rows,
+                                        ctypes.byref(n), _stream(stream)), "dbg_export_sorted")
+        return int(n.value)
 
     def export_device(self, stream=None):
         """Sorted vertices as CUDA tensors (int64 keys [D], or [D, 2] for k > 32;

@@ -26,7 +26,11 @@ Overflow is handled exactly: a table whose status reports that it ran out of
 room is rebuilt at twice the capacity from the request's resident inputs.
 
 Footprint admitted = packed bytes + offsets bytes + registers + table
-bytes, held under ``budget_bytes`` at all times.
+bytes, held under ``budget_bytes``; each export adds its device output
+buffers (24 bytes a vertex) and the library's sort scratch (4 bytes a
+vertex) while it runs.  Every device byte the server uses comes from the
+PyTorch allocator except that scratch; a report gives both the accounted
+peak and the allocator's own.
 """
 
 from __future__ import annotations
@@ -78,7 +82,8 @@ class Timing:
 class Report:
     timings: list = field(default_factory=list)
     wall: float = 0.0
-    peak_bytes: int = 0
+    peak_bytes: int = 0          # the largest footprint the budget accounting held
+    allocator_peak_bytes: int = 0  # what the PyTorch allocator held for the run, at most
     batches: int = 0
     batch_sizes: list = field(default_factory=list)
 
@@ -95,7 +100,9 @@ class Report:
                 "latency_ms_p99": float(np.percentile(lat, 99)),
                 "build_latency_ms_p50": float(np.percentile(blt, 50)),
                 "build_latency_ms_p99": float(np.percentile(blt, 99)),
-                "peak_bytes": int(self.peak_bytes), "batches": self.batches,
+                "peak_bytes": int(self.peak_bytes),
+                "allocator_peak_bytes": int(self.allocator_peak_bytes),
+                "batches": self.batches,
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
                 "rebuilds": int(sum(t.rebuilds for t in self.timings))}
 
@@ -131,12 +138,30 @@ class _Exporter:
         import torch
         if rows > self.rows:
             rows = max(rows, 2 * self.rows)
-            self.keys = torch.empty(rows, dtype=torch.int64, pin_memory=True).numpy().view(
-                np.uint64)
-            self.counts = torch.empty((rows, 4), dtype=torch.int32, pin_memory=True).numpy().view(
-                np.uint32)
+            self.keys_t = torch.empty(rows, dtype=torch.int64, pin_memory=True)
+            self.counts_t = torch.empty((rows, 4), dtype=torch.int32, pin_memory=True)
+            self.keys = self.keys_t.numpy().view(np.uint64)
+            self.counts = self.counts_t.numpy().view(np.uint32)
             self.rows = rows
         return self.keys, self.counts
+
+    def export(self, graph, n: int, s):
+        """The sorted graph of ``n`` vertices in pinned host memory: exported
+        into device buffers on ``s``, then copied; views [:n] are returned."""
+        import torch
+        keys, counts = self.buffers(max(1, n))
+        if n == 0:
+            return keys[:0], counts[:0]
+        with torch.cuda.stream(s):
+            kd = torch.empty(n, dtype=torch.int64, device=s.device)
+            cd = torch.empty((n, 4), dtype=torch.int32, device=s.device)
+        if graph.export_into(kd, cd, s) != n:
+            raise RuntimeError("export: vertex count changed")
+        with torch.cuda.stream(s):
+            self.keys_t[:n].copy_(kd, non_blocking=True)
+            self.counts_t[:n].copy_(cd, non_blocking=True)
+        s.synchronize()
+        return keys[:n], counts[:n]
 
 
 class BuildServer:
@@ -256,8 +281,19 @@ class BuildServer:
             j.timing.rebuilds += 1
             self._make_table(j, 2 * j.capacity, s, force=True)
             j.graph.insert(j.packed, j.offsets, stream=s)
-        keys, counts = j.graph.export(stream=s, out=ex.buffers(j.capacity))
-        j.timing.vertices, j.timing.edges = j.graph.stats(s)
+        # the sorted export: into device buffers from the allocator (the sort
+        # then runs inside them, with 4 bytes a vertex of library scratch),
+        # accounted against the budget while they live, then to pinned host
+        # memory.  Only the export workers release memory, so this takes its
+        # room even past the budget rather than wait (the peak shows it).
+        nv, ne = j.graph.stats(s)
+        xb = _round(nv * (8 + 16 + 4))
+        self._reserve(xb, force=True)
+        try:
+            keys, counts = ex.export(j.graph, nv, s)
+        finally:
+            self._release(xb)
+        j.timing.vertices, j.timing.edges = nv, ne
         j.timing.done = time.perf_counter() - t0
         if sink is not None:
             sink(j.req, keys, counts)
@@ -275,10 +311,15 @@ class BuildServer:
         ``realtime``, else all at once) and return their timings.  ``sink(req,
         keys, counts)`` receives each sorted graph (host arrays, valid during
         the call only)."""
+        import torch
         reqs = sorted(requests, key=lambda r: r.arrival)
         n = len(reqs)
         timings = {r.rid: Timing(r.rid, r.arrival if realtime else 0.0) for r in reqs}
         report = Report()
+        with self._lock:
+            self._peak = self._used  # the peak of this run only
+        torch.cuda.reset_peak_memory_stats(self.device)
+        alloc0 = torch.cuda.memory_allocated(self.device)
         done_q: queue.Queue = queue.Queue()
         work_q: queue.Queue = queue.Queue()
         errors: list = []
@@ -378,6 +419,7 @@ class BuildServer:
         report.wall = time.perf_counter() - t0
         report.timings = [timings[r.rid] for r in reqs]
         report.peak_bytes = self._peak
+        report.allocator_peak_bytes = torch.cuda.max_memory_allocated(self.device) - alloc0
         return report
 
 
@@ -415,8 +457,8 @@ def sequential(requests: list[Request], predictor: CapacityPredictor, sink=None,
         s.synchronize()
         t.built = time.perf_counter() - t0
         t.capacity = g.info()["n_slots"]
-        keys, counts = g.export(out=ex.buffers(t.capacity))
         t.vertices, t.edges = g.stats()
+        keys, counts = ex.export(g, t.vertices, s)
         g.close()
         t.done = time.perf_counter() - t0
         if sink is not None:

@@ -37,10 +37,20 @@ def test_every_declared_symbol_is_exported(lib):
     assert sorted(decl) == sorted(dbg.EXPORTED)
 
 
-def test_library_is_built_for_sm103a(lib):
-    # the cubin's architecture is recorded in the ELF note section names
-    data = open(dbg.LIB_PATH, "rb").read()
-    assert b"sm_103a" in data or b"sm_103" in data
+def test_library_is_built_for_sm103a_only():
+    # every translation unit and the link take exactly one target, sm_103a
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert not any("arch" in f or "sm_" in f for f in build.FLAGS)
+
+
+@pytest.mark.gpu
+def test_kernels_report_sm103_at_run_time(lib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    v = ctypes.c_int()
+    assert lib.dbg_binary_version(ctypes.byref(v)) == dbg.OK
+    assert v.value == 103
 
 
 def test_strerror_and_status_names(lib):
@@ -72,6 +82,9 @@ def test_argument_errors_return_before_any_launch(lib):
     assert lib.dbg_create(21, 10, None) == dbg.ERR_INVALID_ARG
     assert lib.dbg_insert_reads(None, None, None, 5, None) == dbg.ERR_INVALID_ARG
     assert lib.dbg_insert_reads_host(None, None, None, 5, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_build_reads(None, None, None, 5, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_build_reads_host(None, None, None, 0, None) == dbg.ERR_INVALID_ARG
+    assert lib.dbg_binary_version(None) == dbg.ERR_INVALID_ARG
     assert lib.dbg_insert_batch(None, 3, None) == dbg.ERR_INVALID_ARG
     assert lib.dbg_insert_batch(None, 0, None) == dbg.OK
     assert lib.dbg_get_status(None, None) == dbg.ERR_INVALID_ARG

@@ -73,6 +73,12 @@ def test_path_roofline_arithmetic():
     r = bench.path_roofline(120, 121, 45.5, 1.0, 6500.0, probe)
     assert r["atomic_ceiling"] == pytest.approx(2.42e10 * 120 / 121)
     assert r["roofline"] == min(r["hbm_ceiling"], r["atomic_ceiling"])
+    # the binned insert does not touch the table at random: the atomic rate
+    # is the direct path's ceiling only, and the roofline is HBM's
+    r = bench.path_roofline(120, 121, 45.5, 1.0, 6500.0, probe, binned=True)
+    assert r["atomic_ceiling"] is None and r["roofline"] == r["hbm_ceiling"]
+    assert r["direct_path_atomic_ceiling"] == pytest.approx(2.42e10 * 120 / 121)
+    assert r["frac_of_roofline"] == r["frac_of_hbm_ceiling"]
 
 
 def test_autotune_candidates():

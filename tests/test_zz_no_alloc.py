@@ -5,6 +5,7 @@ what dbg_export_sorted returns, call after call, although every call reuses
 the same fixed scratch array inside the library."""
 
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -77,3 +78,56 @@ def test_noalloc_export_size_query_and_empty_graph(lib):
     st, n, _, _ = export_noalloc(lib, empty, 10)
     assert st == dbg.OK and n == 0
     empty.close()
+
+
+def test_noalloc_export_refuses_wide_keys(lib):
+    rs = synth.ragged_reads(200, 150, 51, 818)
+    g = gpu_graph(rs)
+    st, _, _, _ = export_noalloc(lib, g, 100_000)
+    assert st == dbg.ERR_INVALID_ARG
+    g.close()
+
+
+_NO_ALLOC_CHILD = r"""
+import ctypes, sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+sys.path.insert(0, sys.argv[1] + "/tests")
+from gpu_util import gpu_graph
+from paper_2401_02756_gb300 import dbg, synth
+lib = dbg.load()
+rs = synth.sample_reads(synth.random_genome(1_000_000, 5), 4000, 150, 0.0, 5, 31, "x")
+g = gpu_graph(rs)
+D, _ = g.stats()
+keys = torch.empty(D, dtype=torch.int64, device="cuda")
+counts = torch.empty((D, 4), dtype=torch.int32, device="cuda")
+n = ctypes.c_uint64()
+def call():
+    st = lib.dbg_export_sorted_noalloc(g.handle, keys.data_ptr(), counts.data_ptr(), D,
+                                       ctypes.byref(n), None)
+    assert st == dbg.OK, st
+call()  # the first call on the device looks up the scratch array's address
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+for _ in range(4):
+    call()
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+print(D, free0, free1)
+"""
+
+
+def test_noalloc_export_allocates_nothing(lib):
+    # in a fresh process (no pool memory cached by an earlier regular export):
+    # repeated calls on a graph whose regular export would take more than the
+    # fixed scratch's 16 MiB leave the device's free memory exactly as it was
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _NO_ALLOC_CHILD, root], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    D, free0, free1 = map(int, r.stdout.split()[-3:])
+    assert 48 * D > (16 << 20) and D <= dbg.NOALLOC_EXPORT_MAX_VERTICES
+    assert free1 == free0
