@@ -52,10 +52,19 @@ def parse_args():
     ap.add_argument("--downstream", action="store_true",
                     help="also time normalization and contigs on the built table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched-build sub-object out of the default line")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave the request-loop sub-object out of the default line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--tuning", default="",
                     help="insert launch shape, e.g. apply_unroll=4,insert_path=2 (graph unchanged)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="only build the workload's graph warmup + steps times (a small case "
+                         "for ncu) and print a summary line")
+    ap.add_argument("--agg-study", action="store_true",
+                    help="time the direct insert with and without warp aggregation and exit")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="print the random-sector probe rate over buffer sizes and exit")
     ap.add_argument("--window-sweep", action="store_true",
@@ -482,6 +491,32 @@ def run_ours(args):
                       "note": "contig time is the first (sizing) call: marks, starts, sort, "
                               "walk lengths, scan; the second call repeats it and writes"}
     g.close()
+    del packed, offsets
+    torch.cuda.empty_cache()
+
+    # the batched form and the request loop, each with its own clock record
+    # (bounded: a few passes each; --workload batch256 / serve run them alone)
+    batch = serve = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        ck = ClockSampler(dev)
+        ck.start()
+        batch = measure_batch(steps=3, warmup=2)
+        batch["clocks"] = ck.stop()
+        torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_serve:
+        ck = ClockSampler(dev)
+        ck.start()
+        serve = measure_serve(400, 200.0, 150.0, steps=2, overload_rate=2000.0)
+        serve["clocks"] = ck.stop()
+        torch.cuda.empty_cache()
+
+    serve_big = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        ck = ClockSampler(dev)
+        ck.start()
+        serve_big = measure_serve_big(rs)
+        serve_big["clocks"] = ck.stop()
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -524,6 +559,7 @@ def run_ours(args):
             "path_roofline": path_roofline(edges, touches, in_bytes, k1_mean_s, peak, probe,
                                            binned="bin_apply" in kernels),
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+            "batch256": batch, "serve_poisson200": serve, "serve_100mbp_poisson2": serve_big,
             "gpu_launches": sum(v["launches_per_step"] for v in kernels.values()) * K,
             "kernel_source_digest": kernel_source_digest(),
         }
@@ -638,53 +674,73 @@ def measure_batch(steps, warmup, n_samples=256, seed=4):
             size_ms.append(a.elapsed_time(b))
     preds = pred.predict_registers(regs, len(samples))
     graphs = [dbg.Graph(rs.k, pred.capacity(p)) for rs, p in zip(samples, preds)]
-    for rs, g in zip(samples, graphs):
-        # tables large enough for the binned path get an event buffer for all
-        # their vertex positions (high-coverage samples exceed the default of
-        # four per slot and would fall back to the direct insert)
-        if g.info()["table_bytes"] >= (256 << 20):
-            g.reserve_events(int(np.maximum(rs.lengths() - rs.k + 2, 0).sum()))
+    positions = [int(np.maximum(rs.lengths() - rs.k + 2, 0).sum()) for rs in samples]
+    for pos, g in zip(positions, graphs):
+        # every graph asks for event room for all its vertex positions (high-
+        # coverage samples exceed the default of 4.25 per slot): its share of
+        # the library's buffers for a batched build, and for a plain build its
+        # own buffer when its table takes the binned path
+        g.reserve_events(pos)
     items = [(g, pk, of) for g, (pk, of) in zip(graphs, dev_in)]
 
-    def reset_all():
-        for g in graphs:
-            g.reset(stream)
-
+    # a step builds every graph from empty: the batched form with one
+    # dbg_build_batch call (binned chains for the large tables, shared direct
+    # launches for the small ones), the plain form with one dbg_build_reads
+    # per sample
     def batched():
-        dbg.insert_batch(items, stream)
+        dbg.build_batch(items, stream)
 
     def plain():
         for g, (pk, of) in zip(graphs, dev_in):
-            g.insert(pk, of, stream=stream)
+            g.build(pk, of, stream=stream)
 
-    reset_all()
-    batched()  # allocates the binned graphs' scratch before the capture
-    torch.cuda.synchronize()
-    cap_stream = torch.cuda.Stream()
-    cg = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(cg, stream=cap_stream):
-        dbg.insert_batch(items, cap_stream)
-    torch.cuda.synchronize()
+    def capture():
+        batched()  # grows the library's buffers before the capture
+        torch.cuda.synchronize()
+        cap_stream = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap_stream):
+            dbg.build_batch(items, cap_stream)
+        torch.cuda.synchronize()
+        return graph
 
-    results = {}
-    for name, fn in (("batched_graph", cg.replay), ("batched", batched), ("per_sample", plain)):
+    def timed(fn):
         for _ in range(warmup):
-            reset_all()
             fn()
         ms = []
         for _ in range(steps):
-            reset_all()
             a, b = ev(), ev()
             a.record(stream)
             fn()
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
-        results[name] = ms
         for g in graphs:
             if g.status() != dbg.OK:
-                raise RuntimeError(f"{name}: build failed")
+                raise RuntimeError("batch: build failed")
+        return ms
+
+    # the binned chains' shape, picked by the autotuner on this batch (untimed)
+    from paper_2401_02756_gb300 import autotune
+    best, trials = autotune.tune_batch(items, reps=1, stream=stream)
+    results = {}
+    cg = capture()
+    results["batched_graph"] = timed(cg.replay)
+    results["batched"] = timed(batched)
+    results["per_sample"] = timed(plain)
     D = np.array([g.stats()[0] for g in graphs], dtype=np.float64)
+    # the same batch with the single-table choice of path: tables under
+    # 256 MiB on the direct insert (shared launches), the others in chains
+    for g in graphs:
+        if g.info()["table_bytes"] < (256 << 20):
+            g.set_tuning(insert_path=1)
+        else:
+            g.set_tuning(**best)
+    cg_mixed = capture()
+    results["batched_graph_small_direct"] = timed(cg_mixed.replay)
+    for g in graphs:
+        g.set_tuning(**best)
+    del cg, cg_mixed
 
     # without a predictor, plain per-sample launches need the sizes another
     # way: a pilot build of each sample in a table of all its vertex
@@ -729,6 +785,11 @@ def measure_batch(steps, warmup, n_samples=256, seed=4):
                    "sizing": "capacity predictor (margin x 1.5 x predicted vertices)",
                    "l2": "tables emptied between steps; 256 tables total "
                          f"{sum(pred.capacity(p) for p in preds) * 32 / 1e9:.1f} GB > L2"},
+        "tuning": best, "tuning_trials_ms": [[t, ms] for t, ms in trials],
+        "small_direct_edges_per_s":
+            edges / (statistics.mean(results["batched_graph_small_direct"]) / 1e3),
+        "step": "every graph built from empty (dbg_build_batch replayed from a CUDA graph: "
+                "binned chains of up to 128 tables; plain: one dbg_build_reads per sample)",
         "batched_edges_per_s": edges / (bm / 1e3),
         "per_sample_edges_per_s": edges / (pm / 1e3),
         "graph_over_per_sample": pm / gm,
@@ -793,7 +854,23 @@ def measure_serve(n, rate, budget_gb, steps, seed=31, overload_rate=None):
         reqs.append(Request(i, k, pp.numpy(), po.numpy().view(np.uint64), float(t), e))
     edges = sum(r.edges for r in reqs)
     pred = CapacityPredictor()
-    srv = BuildServer(pred, budget_bytes=budget_gb * 1e9)
+    # the chains' shape for this request mix, picked by the autotuner on a
+    # batched build of the first 64 requests (untimed)
+    from paper_2401_02756_gb300 import autotune
+    trial = []
+    for r in reqs[:64]:
+        pk = torch.from_numpy(np.concatenate([r.packed, np.zeros(16, np.uint8)])).cuda()
+        of = torch.from_numpy(r.offsets.view(np.int64).copy()).cuda()
+        g = dbg.Graph(r.k, pred.capacity(pred.predict(r.k, pk, of)))
+        ln = np.diff(r.offsets.astype(np.int64))
+        g.reserve_events(int(np.maximum(ln - r.k + 2, 0).sum()))
+        trial.append((g, pk, of))
+    tuning, _ = autotune.tune_batch(trial, reps=1)
+    for g, _, _ in trial:
+        g.close()
+    del trial
+    torch.cuda.empty_cache()
+    srv = BuildServer(pred, budget_bytes=budget_gb * 1e9, tuning=tuning)
     warm = reqs[:min(16, n)]
     srv.run(warm, realtime=False)
     sequential(warm, pred, realtime=False)
@@ -819,7 +896,8 @@ def measure_serve(n, rate, budget_gb, steps, seed=31, overload_rate=None):
         "config": {"workload": f"serve_poisson{rate:g}", "requests": n, "edges": edges,
                    "arrival_rate_per_s": rate, "budget_gb": budget_gb,
                    "sizes": "batched-build distribution (genome 50 kb-2 Mbp, 10-60x, k 21/31)",
-                   "generation_s": t_gen, "answer": "sorted graph exported to host memory"},
+                   "generation_s": t_gen, "answer": "sorted graph exported to host memory",
+                   "tuning": tuning},
         "latency_ms_p50": live["latency_ms_p50"], "latency_ms_p99": live["latency_ms_p99"],
         "build_latency_ms_p50": live["build_latency_ms_p50"],
         "build_latency_ms_p99": live["build_latency_ms_p99"],
@@ -829,6 +907,43 @@ def measure_serve(n, rate, budget_gb, steps, seed=31, overload_rate=None):
                        "latency_ms_p99": live_seq["latency_ms_p99"], "realtime": live_seq},
         "server_over_sequential": thr / thr_seq,
     }
+
+
+def measure_serve_big(rs, n=6, rate=2.0, budget_gb=150.0, seed=33):
+    """The request loop on requests the size of the 100 Mbp workload (2.4e9
+    edges each, all the same reads) arriving at a low Poisson rate: each
+    request's table is far beyond what the capacity network was trained on,
+    so HyperLogLog sizes it; the binned chain builds it; the answer is its
+    sorted graph (422 M vertices) in host memory.  Beside it, the same
+    requests served one at a time with plain calls.  Returns a dict."""
+    import torch
+
+    from paper_2401_02756_gb300 import synth
+    from paper_2401_02756_gb300.predictor import CapacityPredictor
+    from paper_2401_02756_gb300.serve import BuildServer, Request, sequential
+    pp = torch.empty(rs.packed.size, dtype=torch.uint8, pin_memory=True)
+    pp.numpy()[:] = rs.packed
+    po = torch.empty(rs.offsets.size, dtype=torch.int64, pin_memory=True)
+    po.numpy()[:] = rs.offsets.view(np.int64)
+    packed, offsets = pp.numpy(), po.numpy().view(np.uint64)
+    arrivals = synth.poisson_arrivals(n, rate, seed)
+    reqs = [Request(i, rs.k, packed, offsets, float(t), rs.n_edges()) for i, t in enumerate(arrivals)]
+    pred = CapacityPredictor()
+    srv = BuildServer(pred, budget_bytes=budget_gb * 1e9, max_batch=4)
+    srv.run(reqs[:1], realtime=False)  # buffers (library chain, pinned export) grown once
+    live = srv.run(reqs, realtime=True).summary()
+    seq = sequential(reqs[:2], pred, realtime=False).summary()
+    return {"config": {"workload": f"serve_100mbp_poisson{rate:g}", "requests": n,
+                       "edges_per_request": rs.n_edges(), "arrival_rate_per_s": rate,
+                       "budget_gb": budget_gb,
+                       "sizing": "HyperLogLog (beyond the network's training range)",
+                       "answer": "sorted graph exported to host memory"},
+            "latency_ms_p50": live["latency_ms_p50"], "latency_ms_p99": live["latency_ms_p99"],
+            "build_latency_ms_p50": live["build_latency_ms_p50"],
+            "build_latency_ms_p99": live["build_latency_ms_p99"],
+            "mean_batch": live["mean_batch"], "peak_bytes": live["peak_bytes"],
+            "allocator_peak_bytes": live["allocator_peak_bytes"], "realtime": live,
+            "sequential_one_at_a_time_ms": seq["wall_s"] * 1e3 / 2}
 
 
 def run_serve(args):
@@ -843,6 +958,104 @@ def run_serve(args):
             "data": "synthetic", "config": sv["config"], "clocks": clock_info}
     line.update({k: v for k, v in sv.items() if k not in ("config", "edges_per_s", "ms_per_pass")})
     print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """Build the workload's graph (dbg_build_reads, the benchmark's step)
+    warmup + steps times with the given tuning, check it, print one line:
+    the command profilers run (one kernel at a time, on a small workload)."""
+    import torch
+
+    from paper_2401_02756_gb300 import build as _build
+    from paper_2401_02756_gb300 import dbg, synth
+    _build.build()
+    dbg.load()
+    torch.cuda.set_device(0)
+    rs = synth.WORKLOADS[args.workload]()
+    packed = torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda()
+    offsets = torch.from_numpy(rs.offsets.view(np.int64).copy()).cuda()
+    touches = int(np.maximum(rs.lengths() - rs.k + 2, 0).sum())
+    D = workload_distinct(args.workload)
+    if D is None:
+        pilot = dbg.Graph(rs.k, int(touches * 1.05) + 1024)
+        pilot.insert(packed, offsets)
+        D, _ = pilot.stats()
+        pilot.close()
+    g = dbg.Graph(rs.k, int(math.ceil(1.5 * D)))
+    tuning = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.tuning.split(",") if kv}
+    if tuning:
+        g.set_tuning(**tuning)
+    for _ in range(args.warmup + args.steps):
+        g.build(packed, offsets)
+    torch.cuda.synchronize()
+    nv, ne = g.stats()
+    if g.status() != dbg.OK or nv != D or ne != rs.n_edges():
+        raise RuntimeError("profile case: wrong graph")
+    print(json.dumps({"workload": args.workload, "tuning": tuning or "default", "builds":
+                      args.warmup + args.steps, "vertices": nv, "edges": ne, "touches": touches,
+                      "table_slots": g.info()["n_slots"], "binned": g.binned_counters()}),
+          flush=True)
+    g.close()
+
+
+def microsatellite_reads(n_per_period=20000, read_len=150, seed=5):
+    """Low-complexity reads: a random unit of 1..6 bases repeated over the
+    whole read (microsatellites), n_per_period reads per unit length -- every
+    warp of the direct insert then sees the same few keys many times."""
+    from paper_2401_02756_gb300 import synth
+    reads = []
+    for period in range(1, 7):
+        u = synth.draws(seed, 90 + period, n_per_period * period)
+        units = (u % 4).astype(np.uint8).reshape(n_per_period, period)
+        for unit in units:
+            reads.append(synth.codes_to_ascii(np.resize(unit, read_len)))
+    return synth.from_strings(reads, 31, "microsatellites")
+
+
+def run_agg_study(args):
+    """The direct insert (insert_path = 1) with warp aggregation off and on
+    (__match_any_sync on the key, then on (slot, label)): the 100 Mbp
+    workload, where a warp's 32 positions are 32 consecutive k-mers of one
+    read (distinct keys), and microsatellite reads, where they repeat.  One
+    JSON line per (workload, setting): mean build ms over the steps."""
+    import torch
+
+    from paper_2401_02756_gb300 import build as _build
+    from paper_2401_02756_gb300 import dbg, synth
+    _build.build()
+    dbg.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    for name in ("100mbp_30x_k31", "microsatellites"):
+        rs = synth.WORKLOADS[name]() if name in synth.WORKLOADS else microsatellite_reads()
+        packed = torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda()
+        offsets = torch.from_numpy(rs.offsets.view(np.int64).copy()).cuda()
+        touches = int(np.maximum(rs.lengths() - rs.k + 2, 0).sum())
+        D = workload_distinct(name)
+        cap = int(math.ceil(1.5 * D)) if D else max(1024, touches // 4)
+        g = dbg.Graph(rs.k, cap)
+        ref = None
+        for agg in (0, 1):
+            g.set_tuning(insert_path=1, warp_aggregate=agg)
+            for _ in range(args.warmup):
+                g.build(packed, offsets, stream=stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                g.build(packed, offsets, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            st = g.stats()
+            ref = ref or st
+            if g.status() != dbg.OK or st != ref:
+                raise RuntimeError(f"{name}: build differs with warp_aggregate={agg}")
+            ms = a.elapsed_time(b) / args.steps
+            print(json.dumps({"workload": name, "warp_aggregate": agg, "build_ms": ms,
+                              "edges": rs.n_edges(), "edges_per_s": rs.n_edges() / (ms / 1e3),
+                              "distinct_vertices": st[0], "table_slots": cap}), flush=True)
+        g.close()
+        del packed, offsets
+        torch.cuda.empty_cache()
 
 
 def run_probe_sweep(window_only=False):
@@ -895,6 +1108,10 @@ def main():
     args = parse_args()
     if args.probe_sweep or args.window_sweep:
         run_probe_sweep(window_only=args.window_sweep)
+    elif args.agg_study:
+        run_agg_study(args)
+    elif args.profile_case:
+        run_profile_case(args)
     elif args.workload == "batch256" and args.impl == "ours":
         run_batch(args)
     elif args.workload == "serve" and args.impl == "ours":

@@ -78,6 +78,9 @@ typedef struct dbg_tuning {
   int region_log2;    /* binned: table region of 2^region_log2 slots, 16..26 (0: automatic) */
   int apply_group;    /* binned apply (streaming): regions per launch (0: all in one launch) */
   int apply_mode;     /* binned apply: 0 automatic (tiled), 1 streaming, 2 tiled */
+  int scatter_reads;  /* binned scatter (tiled apply): reads per read tile, 32..512 (0: 416) */
+  int split_threads;  /* binned split: threads per CTA, 256, 512 or 1024, at least a quarter
+                         of the tiles per region (0: automatic) */
 } dbg_tuning;
 
 typedef struct dbg_info {
@@ -137,13 +140,15 @@ int dbg_set_tuning(dbg_handle h, const dbg_tuning *t);
 
 /* Size the binned insert's event buffers for `events` vertex positions per
  * call, plus a margin for the per-region buckets (events / 16 + 589,824;
- * 0 = the default of 4.25 per table slot), allocating the first (8 bytes per
- * event) now; the tiled apply adds a second one, 1.125 times as large plus
- * 2^20 events (room for its per-tile buckets), on its first call.  Read sets with more positions per slot than the buffer allows
- * (high coverage into a tight table) should reserve their position count,
- * sum over reads of max(0, length - k + 2); otherwise those calls take the
- * direct insert.  Synchronizes the device if the buffer grows.  Errors:
- * INVALID_ARG, OOM. */
+ * 0 = the default of 4.25 per table slot).  The handle's first buffer (8
+ * bytes per event) is allocated by its next single-read-set binned insert,
+ * the second (1.125 times as large plus 2^20 events: room for the per-tile
+ * buckets) with it; a batched insert instead counts this size towards the
+ * library's own buffers.  Read sets with more positions per slot than the
+ * buffer allows (high coverage into a tight table) should reserve their
+ * position count, sum over reads of max(0, length - k + 2); otherwise those
+ * calls take the direct insert.  Synchronizes the device when it drops a
+ * buffer of another size.  Errors: INVALID_ARG, CUDA. */
 int dbg_reserve_events(dbg_handle h, uint64_t events);
 
 /* Measurement aid: record CUDA events around every kernel of the next insert
@@ -244,18 +249,51 @@ typedef struct dbg_batch_item {
 } dbg_batch_item;
 
 /* Insert many independent read sets, each into its own graph (graphs may
- * differ in k and size).  Graphs small enough for the direct path share
- * launches: one kernel for up to 128 of them, its CTAs taking (item, read
- * tile) work units from one index space.  Graphs that take the binned path
- * (see dbg_insert_reads) are inserted with it, one after another.  Every graph
- * must live on the current device; all work is on `stream`.  The result equals
- * one dbg_insert_reads per item.  The call may be captured into a CUDA graph
- * (cudaStreamBeginCapture on `stream`) once every binned graph's scratch
- * exists (dbg_reserve_events, or one uncaptured call); replays of the graph
- * must then not overlap other binned inserts into the same graphs.
+ * differ in k and size), as one dbg_insert_reads per item would (Alg. 2 per
+ * read set).  Graphs with k <= 31 are inserted together in binned chains
+ * (see dbg_insert_reads for the binned path), whatever their size, unless
+ * their tuning asks for the direct path (insert_path = 1): every binned
+ * kernel is launched once per chain and covers all of the chain's tables --
+ * the scatter takes (item, read tile) work units of every read set, the
+ * regions of all tables share one event buffer, the split and the tiled
+ * apply take every table's regions and tiles.  A chain holds up to 128
+ * graphs, 2048 table regions (2^21 slots each, by default) and 3.8e9 events;
+ * its event buffer holds the sum of its graphs' dbg_reserve_events sizes (or
+ * defaults), and if the events do not fit it, the direct insert does that
+ * chain's work (decided on the device).  The chains' buffers belong to the
+ * library, one set per device, grown as needed and kept until
+ * dbg_release_scratch; batched calls on one device run one after another on
+ * the GPU.  Graphs on the direct path (and k = 32) share launches: one
+ * kernel for up to 128 of them, its CTAs taking (item, read tile) work units
+ * from one index space.  Graphs with k > 32 take their own kernel one by
+ * one.  Every graph
+ * must live on the current device; all work is on `stream`.  The call may be
+ * captured into a CUDA graph (cudaStreamBeginCapture on `stream`) after one
+ * uncaptured call with graphs of the same sizes (which grows the buffers; a
+ * captured call finding them too small gives its chains to the direct
+ * insert); replays must not overlap other batched calls on the device.
  * Errors: INVALID_ARG, OOM, CUDA; sticky errors are recorded in each item's
  * own graph. */
 int dbg_insert_batch(const dbg_batch_item *items, int n_items, void *stream);
+
+/* dbg_build_reads for many read sets: every item's graph is emptied (table,
+ * sticky status, spill records) and built from its reads, with the batching
+ * of dbg_insert_batch.  In the binned chains the emptying is folded into the
+ * tiled apply (no pass of its own); direct-path graphs are emptied by one
+ * launch per group of 128.  Errors: as dbg_insert_batch. */
+int dbg_build_batch(const dbg_batch_item *items, int n_items, void *stream);
+
+/* Give back the device memory the library keeps between calls: the batched
+ * inserts' buffers and the export's cached temporary memory, on every device
+ * (each is synchronised first).  Later calls allocate again as needed.
+ * Errors: CUDA. */
+int dbg_release_scratch(void);
+
+/* Device bytes the library holds between calls on the current device: the
+ * batched inserts' buffers and the export's cached temporary memory (what
+ * dbg_release_scratch gives back).  A caller that keeps a device-memory
+ * budget counts them; 0 when there is no device. */
+uint64_t dbg_scratch_bytes(void);
 
 /* Grow-and-rebuild.  dbg_set_spill gives the graph a buffer of `records`
  * 16-byte spill records (0 removes it): a vertex position that finds no
@@ -302,6 +340,27 @@ int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *strea
  * BUFFER_TOO_SMALL, and the sticky status (nothing exported when it is set). */
 int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, uint64_t max_n,
                       uint64_t *n_out, void *stream);
+
+/* Device bytes of scratch dbg_export_sorted_with needs for a graph of
+ * n_vertices vertices (k <= 32, a table of at most 2^32 slots): the sort's
+ * histograms and one slot index per vertex.  0 for arguments it does not
+ * take.  Needs a device (the sort sizes its work for it). */
+uint64_t dbg_export_scratch_bytes(int k, uint64_t n_vertices, uint64_t n_slots);
+
+/* dbg_export_sorted with every byte of device memory from the caller: for a
+ * caller that keeps its own budget of device memory (a request loop that
+ * accounts for each request's footprint) and wants none taken from the
+ * library's pool.  keys_out (uint64 [n]) and counts_out (uint32 [n][4]) are
+ * 16-byte aligned DEVICE buffers -- the sort runs inside them -- and
+ * `scratch` is a 256-byte aligned device buffer of at least
+ * dbg_export_scratch_bytes(k, n, n_slots) bytes, all owned by the caller.
+ * k <= 32 and a table of at most 2^32 slots.  Same result and ordering as
+ * dbg_export_sorted; waits for `stream`.  Errors: INVALID_ARG (including too
+ * small or misaligned scratch and host outputs), CUDA, BUFFER_TOO_SMALL (a
+ * size query with max_n = 0), and the sticky status. */
+int dbg_export_sorted_with(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out,
+                           uint64_t max_n, uint64_t *n_out, void *scratch,
+                           uint64_t scratch_bytes, void *stream);
 
 /* Normalization (Section "Normalization of graph"): every counter c of the
  * graph becomes floor(c / divisor + 0.5), computed in IEEE double and capped

@@ -33,6 +33,8 @@
 // every later binned kernel returns at once and the direct insert kernel,
 // launched last with the same flag as its gate, does the work instead.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "dbg_binned.cuh"
 #include "dbg_tiles.cuh"
@@ -43,6 +45,31 @@ namespace {
 
 constexpr int kMaxParts = kBinMaxParts;
 constexpr int kRun = 8;             // consecutive vertex positions per thread (rolled keys)
+
+constexpr int kTileLog2 = 11;
+constexpr int kTileSlots = 1 << kTileLog2;  // 2048 slots = 64 KB of shared memory
+constexpr int kMaxTilesPerRegion = 4096;    // beyond this the streaming apply is used
+constexpr int kTiledShift = 21;             // automatic regions of the tiled path: 1024 tiles
+
+// The tiled path's bookkeeping for one chain of items (one or many tables).
+// Regions never span two tables: item i's table is cut into regions
+// region0_i, region0_i + 1, ... of 2^shift slots (the last one shorter), and
+// every region into tiles of kTileSlots slots (the last one shorter).  Tiles
+// are numbered compactly, region after region.
+struct TileAux {
+  unsigned long long *unit_base;     // [parts + 1] units of the regions before p
+  unsigned long long *region_base;   // [parts + 1] region p's first bucket; [parts]: overflow area
+  uint32_t *tile_cap;                // [parts] events one tile bucket of region p holds
+  uint32_t *fill;                    // [tiles] events each tile received (zeroed per call)
+  uint32_t *region_item;             // [parts] the item (table) of region p
+  unsigned long long *region_first;  // [parts] region p's first slot in its table
+  unsigned long long *region_nslots; // [parts] slots of that table
+  uint32_t *region_tile0;            // [parts + 1] compact index of region p's first tile
+  uint16_t *tile_region;             // [tiles] region of every tile (chains of many tables)
+  unsigned long long *deferred_n;    // [parts] events of region p whose probe left their tile
+  unsigned long long *overflow;      // [1] events in the overflow area
+  unsigned long long *deferred;      // [1] events whose probe left their tile, in all
+};
 
 __device__ __forceinline__ uint64_t make_event(uint64_t key, bool edge, uint32_t label) {
   return (key << 3) | ((uint64_t)edge << 2) | (uint64_t)label;
@@ -166,9 +193,22 @@ __global__ void __launch_bounds__(1024)
 // keys) clears the use-binned flag, and the direct insert does the call
 // instead, exactly as when the events exceed the buffer.
 
-// *total = vertex positions of the read set, sum of max(0, len - k + 2).
-__global__ void k_bin_total(const uint64_t *offsets, uint64_t n_reads, int k,
-                            unsigned long long *total) {
+// totals[i] = vertex positions of item i's reads, sum of max(0, len - k + 2)
+// (grid: x strides over the item's reads, y = item).
+// clear: also zero every item's sticky status and spill count (a rebuild
+// from empty; this is the chain's first kernel, so every later one sees it).
+template <int N>
+__global__ void k_bin_totals(const __grid_constant__ ItemPack<N> pk, unsigned long long *totals,
+                             int clear) {
+  const int i = blockIdx.y;
+  if (i >= pk.n_items) return;
+  if (clear && blockIdx.x == 0 && threadIdx.x == 0) {
+    *pk.d[i].status = 0u;
+    *pk.d[i].spill_count = 0ull;
+  }
+  const uint64_t *offsets = pk.d[i].offsets;
+  const uint64_t n_reads = pk.d[i].n_reads;
+  const int k = pk.d[i].k;
   unsigned long long v = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += stride) {
@@ -177,30 +217,14 @@ __global__ void k_bin_total(const uint64_t *offsets, uint64_t n_reads, int k,
     v += len >= (uint64_t)k ? len - k + 2 : 0;
   }
   for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(&totals[i], v);
 }
 
-// One CTA of 1024 threads (two regions each): bucket p starts at begin[p]
-// and holds its expected events plus the margin; cursor[p] = begin[p];
-// the flag says whether all buckets fit the buffer; resets the scatter's
-// slice counter.
-__global__ void __launch_bounds__(1024)
-    k_bin_buckets(const unsigned long long *total, uint64_t n_slots, int shift, int parts,
-                  unsigned long long *begin, unsigned long long *cursor, uint64_t cap,
-                  unsigned long long *ctr, uint32_t *use_binned) {
-  __shared__ unsigned long long s_warp[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double E = (double)*total;
-  auto bucket = [&](int p) -> unsigned long long {
-    if (p >= parts) return 0ull;
-    const uint64_t first = (uint64_t)p << shift;
-    const uint64_t slots = min((uint64_t)1 << shift, n_slots - first);
-    const double expected = E * (double)slots / (double)n_slots;
-    return (unsigned long long)ceil(expected * 1.03 + 16.0 * sqrt(expected) + 256.0);
-  };
-  const int p0 = 2 * tid;
-  const unsigned long long ca = bucket(p0), cb = bucket(p0 + 1);
-  const unsigned long long local = ca + cb;
+// Exclusive prefix over a CTA of 1024 threads; `total` receives the sum.
+__device__ __forceinline__ unsigned long long cta1024_exclusive_scan(unsigned long long local,
+                                                                     unsigned long long *s_warp,
+                                                                     unsigned long long &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long incl = local;
   for (int d = 1; d < 32; d <<= 1) {
     const unsigned long long o = __shfl_up_sync(kFull, incl, d);
@@ -217,12 +241,64 @@ __global__ void __launch_bounds__(1024)
     s_warp[lane] = w;
   }
   __syncthreads();
-  const unsigned long long b = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
-  if (p0 < parts) begin[p0] = cursor[p0] = b;
-  if (p0 + 1 < parts) begin[p0 + 1] = cursor[p0 + 1] = b + ca;
+  const unsigned long long ex = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
+  total = s_warp[31];
+  __syncthreads();  // s_warp is free again
+  return ex;
+}
+
+// One CTA of 1024 threads (two regions each).  Region p belongs to the last
+// item i with region0 <= p; it covers slots [first, first + slots) of that
+// item's table and ceil(slots / kTileSlots) tiles.  Its bucket holds its
+// share of the item's vertex positions plus the margin, and starts at
+// begin[p]; cursor[p] = begin[p].  The region table (item, first slot, table
+// size, first tile) is written for the later passes.  The flag says whether
+// all buckets fit the buffer; the scatter's slice counter is reset.
+template <int N>
+__global__ void __launch_bounds__(1024)
+    k_bin_buckets(const __grid_constant__ ItemPack<N> pk, const unsigned long long *totals,
+                  int shift, int parts, unsigned long long *begin, unsigned long long *cursor,
+                  uint64_t cap, unsigned long long *ctr, uint32_t *use_binned, TileAux aux) {
+  __shared__ unsigned long long s_warp[32];
+  const int tid = threadIdx.x;
+  unsigned long long bk[2], nt[2];
+  for (int j = 0; j < 2; ++j) {
+    const int p = 2 * tid + j;
+    bk[j] = nt[j] = 0ull;
+    if (p >= parts) continue;
+    int lo = 0, hi = pk.n_items - 1;  // the last item whose first region is <= p
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pk.d[mid].region0 <= p)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const uint64_t ns = pk.d[lo].n_slots;
+    const uint64_t first = (uint64_t)(p - pk.d[lo].region0) << shift;
+    const uint64_t slots = min((uint64_t)1 << shift, ns - first);
+    const double expected = (double)totals[lo] * (double)slots / (double)ns;
+    bk[j] = (unsigned long long)ceil(expected * 1.03 + 16.0 * sqrt(expected) + 256.0);
+    nt[j] = (slots + kTileSlots - 1) >> kTileLog2;
+    aux.region_item[p] = (uint32_t)lo;
+    aux.region_first[p] = first;
+    aux.region_nslots[p] = ns;
+  }
+  unsigned long long all, tiles;
+  const unsigned long long b = cta1024_exclusive_scan(bk[0] + bk[1], s_warp, all);
+  const unsigned long long t0 = cta1024_exclusive_scan(nt[0] + nt[1], s_warp, tiles);
+  const int p0 = 2 * tid;
+  if (p0 < parts) {
+    begin[p0] = cursor[p0] = b;
+    aux.region_tile0[p0] = (uint32_t)t0;
+  }
+  if (p0 + 1 < parts) {
+    begin[p0 + 1] = cursor[p0 + 1] = b + bk[0];
+    aux.region_tile0[p0 + 1] = (uint32_t)(t0 + nt[0]);
+  }
   if (tid == 0) {
-    const unsigned long long all = s_warp[31];
     begin[parts] = all;
+    aux.region_tile0[parts] = (uint32_t)tiles;
     *use_binned = all <= cap ? 1u : 0u;
     ctr[1] = 0;
   }
@@ -289,7 +365,7 @@ struct ScatterVisitor {
   __device__ void vertex(bool valid, uint64_t key, bool edge, uint32_t label, int, int sub,
                          const VertexCtx &c) {
     if (valid) {
-      const uint32_t p = (uint32_t)(home_slot(key, c.n_slots) >> shift);
+      const uint32_t p = (uint32_t)c.region0 + (uint32_t)(home_slot(key, c.n_slots) >> shift);
       ev[sub] = make_event(key, edge, label);
       where[sub] = (p << 16) | atomicAdd(&hist[p], 1u);
     } else {
@@ -350,15 +426,19 @@ struct ScatterVisitor {
 
 constexpr int kScatterTileReads = 416;  // reads per scatter tile without a count pass (<= 512)
 
+int scatter_tile_reads(const dbg_tuning &t) {
+  return t.scatter_reads > 0 ? t.scatter_reads : kScatterTileReads;
+}
+
 template <int BLOCK>
 constexpr size_t scatter_smem(int tile_reads, int parts) {
   return tile_smem_bytes(tile_reads) + (size_t)BLOCK * kRun * (8 + 2) +
          (size_t)parts * (4 + 4 + 8 + 8) + 64;
 }
 
-template <int BLOCK>
+template <int BLOCK, int N>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
-    k_bin_scatter(const __grid_constant__ ItemPack<1> pk, int tile_reads, int shift, int parts,
+    k_bin_scatter(const __grid_constant__ ItemPack<N> pk, int tile_reads, int shift, int parts,
                   uint64_t slices, const uint32_t *hist, unsigned long long *cursor, uint64_t *out,
                   uint64_t cap, unsigned long long *ctr, uint32_t *use_binned,
                   const unsigned long long *bucket_end) {
@@ -399,7 +479,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
       }
     }
     __syncthreads();
-    for_each_vertex<BLOCK, 1, kRun>(pk, tile_reads, smem, vis, sl * T / slices,
+    for_each_vertex<BLOCK, N, kRun>(pk, tile_reads, smem, vis, sl * T / slices,
                                     (sl + 1) * T / slices, 1);
   }
 }
@@ -584,62 +664,21 @@ __global__ void __launch_bounds__(BLOCK)
 // as in the direct insert, so every key stays within max_probes of its home
 // slot.
 
-constexpr int kTileLog2 = 11;
-constexpr int kTileSlots = 1 << kTileLog2;  // 2048 slots = 64 KB of shared memory
-constexpr int kMaxTilesPerRegion = 4096;    // beyond this the streaming apply is used
-constexpr int kTiledShift = 21;             // automatic regions of the tiled path: 1024 tiles
-
 constexpr int kBatch = 8;  // events each thread loads before it uses them (memory parallelism)
 
-struct TileAux {
-  unsigned long long *unit_base;    // [parts + 1] units of the regions before p
-  unsigned long long *region_base;  // [parts + 1] region p's first bucket; [parts]: overflow area
-  uint32_t *tile_cap;               // [parts] events one tile bucket of region p holds
-  uint32_t *fill;                   // [parts * tpr] events each tile received (zeroed per call)
-  unsigned long long *overflow;     // [1] events in the overflow area
-  unsigned long long *deferred;     // [1] events whose probe left their tile
-};
-
-// Exclusive prefix over a CTA of 1024 threads; `total` receives the sum.
-__device__ __forceinline__ unsigned long long cta1024_exclusive_scan(unsigned long long local,
-                                                                     unsigned long long *s_warp,
-                                                                     unsigned long long &total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long incl = local;
-  for (int d = 1; d < 32; d <<= 1) {
-    const unsigned long long o = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += o;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned long long w = s_warp[lane];
-    for (int d = 1; d < 32; d <<= 1) {
-      const unsigned long long o = __shfl_up_sync(kFull, w, d);
-      if (lane >= d) w += o;
-    }
-    s_warp[lane] = w;
-  }
-  __syncthreads();
-  const unsigned long long ex = incl - local + (warp > 0 ? s_warp[warp - 1] : 0ull);
-  total = s_warp[31];
-  __syncthreads();  // s_warp is free again
-  return ex;
-}
 
 // One CTA of 1024 threads, two regions each.  Region p's events are those
 // its bucket received (cursor - begin); they become counts[p] and are cut
 // into ceil(count / unit) units (unit_base, a prefix).  The region's tiles
-// that lie inside the table (rt of them) get buckets of mean + slack events,
+// (rt of them, from the region table) get buckets of mean + slack events,
 // mean = count / rt, slack = 3 % + 16 sqrt(mean) + 64 (a tile's count varies
 // with its keys' multiplicities, as a region's does; at the 100 Mbp, 30x
 // workload 0.1 % of the events overflow).  If the buckets and an overflow area of 1/64 of the
 // buffer do not fit the buffer, the slack shrinks first, then the buckets.
 __global__ void __launch_bounds__(1024)
     k_tile_units(unsigned long long *counts, const unsigned long long *begin,
-                 const unsigned long long *cursor, int parts, int shift, int tpr,
-                 uint64_t n_slots, uint64_t unit, uint64_t ev2_cap, TileAux aux,
-                 const uint32_t *use_binned) {
+                 const unsigned long long *cursor, int parts, uint64_t unit, uint64_t ev2_cap,
+                 TileAux aux, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   __shared__ double s_red[3][32];
   __shared__ unsigned long long s_warp[32];
@@ -656,8 +695,7 @@ __global__ void __launch_bounds__(1024)
     if (p < parts) {
       n[i] = cursor[p] - begin[p];
       counts[p] = n[i];
-      const uint64_t left = (n_slots - ((uint64_t)p << shift) + kTileSlots - 1) >> kTileLog2;
-      rt[i] = (uint32_t)min((uint64_t)tpr, left);
+      rt[i] = aux.region_tile0[p + 1] - aux.region_tile0[p];
       if (n[i]) {
         mean[i] = (double)n[i] / (double)rt[i];
         slack[i] = 0.03 * mean[i] + 16.0 * sqrt(mean[i]) + 64.0;
@@ -709,6 +747,10 @@ __global__ void __launch_bounds__(1024)
     *aux.overflow = 0ull;
     *aux.deferred = 0ull;
   }
+  for (int i = 0; i < 2; ++i) {
+    const int p = 2 * tid + i;
+    if (p < parts) aux.deferred_n[p] = 0ull;
+  }
 }
 
 // Region of unit u (the last p with unit_base[p] <= u) and its event range.
@@ -725,10 +767,12 @@ __device__ __forceinline__ int unit_region(const unsigned long long *unit_base, 
   return lo;
 }
 
-__device__ __forceinline__ uint32_t tile_in_region(uint64_t ev, uint64_t n_slots, int shift,
-                                                   int p) {
+// Tile of an event inside its region: its home slot in the region's table
+// (n_slots slots), relative to the region's first tile.
+__device__ __forceinline__ uint32_t tile_in_region(uint64_t ev, uint64_t n_slots,
+                                                   uint64_t first_tile) {
   const uint64_t home = home_slot(ev >> 3, n_slots);
-  return (uint32_t)((home >> kTileLog2) - ((uint64_t)p << (shift - kTileLog2)));
+  return (uint32_t)((home >> kTileLog2) - first_tile);
 }
 
 // kBatch events of [base, b) strided by BLOCK, kEmpty past b (never an event:
@@ -800,8 +844,7 @@ template <int BLOCK, bool STAGED>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threads per SM
     k_tile_scatter(const uint64_t *__restrict__ ev, uint64_t *__restrict__ ev2, uint64_t ev2_cap,
                    const unsigned long long *begin, const unsigned long long *counts, TileAux aux,
-                   int parts, uint64_t unit, int shift, int tpr, uint64_t n_slots,
-                   uint32_t *status, uint32_t *use_binned) {
+                   int parts, uint64_t unit, int tpr, uint32_t *status, uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   constexpr int C = BLOCK * kBatch;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -819,8 +862,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threa
   const int tid = threadIdx.x;
   const int per = (tpr + BLOCK - 1) / BLOCK;  // bins per thread in the prefix
   const int j0 = min(tpr, tid * per), j1 = min(tpr, j0 + per);
+  // the overflow area holds (event, region) pairs
   const uint64_t over_base = aux.region_base[parts];
-  const uint64_t over_cap = ev2_cap > over_base ? ev2_cap - over_base : 0ull;
+  const uint64_t over_cap = ev2_cap > over_base ? (ev2_cap - over_base) / 2 : 0ull;
   uint64_t *over = ev2 + over_base;
   if (STAGED && tid == 0) {
     mbar_init(&s_bar, 1);
@@ -835,8 +879,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threa
   uint32_t parity = 0;
   while (have) {
     const uint32_t cap = aux.tile_cap[c.p];
-    uint32_t *fill = aux.fill + (uint64_t)c.p * tpr;
+    uint32_t *fill = aux.fill + aux.region_tile0[c.p];
     uint64_t *out = ev2 + aux.region_base[c.p];
+    const uint64_t ns = aux.region_nslots[c.p];
+    const uint64_t first_tile = aux.region_first[c.p] >> kTileLog2;
     // (the previous chunk's write-out reads no s_hist: no barrier before this)
     for (int j = tid; j < tpr; j += BLOCK) s_hist[j] = 0u;
     __syncthreads();
@@ -858,7 +904,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threa
 #pragma unroll
     for (int r = 0; r < kBatch; ++r) {
       if (e[r] != kEmpty) {
-        const uint32_t t = tile_in_region(e[r], n_slots, shift, c.p);
+        const uint32_t t = tile_in_region(e[r], ns, first_tile);
         where[r] = (t << 16) | atomicAdd(&s_hist[t], 1u);
       }
     }
@@ -940,7 +986,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)  // two CTAs of 512 threa
         out[(uint64_t)s_at[t] + r] = s_ev[i];
       } else {
         const uint32_t o = s_ovf[t];
-        if (o != ~0u) over[(uint64_t)o + (r - fit)] = s_ev[i];
+        if (o != ~0u) {
+          uint64_t *rec = over + 2 * ((uint64_t)o + (r - fit));
+          rec[0] = s_ev[i];
+          rec[1] = (uint64_t)c.p;
+        }
       }
     }
     c = nx;
@@ -975,7 +1025,9 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, ui
                                            int len, uint64_t n_slots, uint32_t max_probes,
                                            uint32_t *status, SpillRecord *spill,
                                            uint64_t spill_cap, unsigned long long *spill_count,
-                                           uint64_t *deferred_ev, unsigned long long *deferred) {
+                                           int p, uint64_t *ev,
+                                           const unsigned long long *begin,
+                                           unsigned long long *deferred_n) {
   const unsigned long long key = e >> 3;
   const uint64_t h = key_hash(key);
   const int home = (int)(__umul64hi(h, n_slots) - first);  // = home_slot(key) - first
@@ -995,14 +1047,13 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, ui
     }
     const int i = (__ffs(cand) >> 3) - 1;  // the first candidate's byte
     const int sl = q + i;
-    bool found;
-    if (((w >> (8 * i)) & 0xFFu) == 0u) {  // empty (as far as the byte knows): claim it
-      const unsigned long long prev = atomicCAS(&st[sl].key, kEmpty, key);
-      if (prev == kEmpty) fp[sl] = (uint8_t)f;
-      found = prev == kEmpty || prev == key;
-    } else {
-      found = st[sl].key == key;
-    }
+    // one shared-memory CAS for every candidate: it claims an empty slot and
+    // returns an occupied slot's key, so found, claimed and another key take
+    // one path (measured faster than a load for the byte matches and a CAS
+    // for the empty bytes, whose paths diverge)
+    const unsigned long long prev = atomicCAS(&st[sl].key, kEmpty, key);
+    if (prev == kEmpty) fp[sl] = (uint8_t)f;
+    const bool found = prev == kEmpty || prev == key;
     if (found) {
       if (e & 4ull) atomicAdd(&st[sl].cnt[e & 3ull], 1u);
       return;
@@ -1013,20 +1064,34 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, ui
     spill_or_fail(spill, spill_cap, spill_count, status, key, (e & 4ull) != 0,
                   (uint32_t)(e & 3ull));
   else
-    deferred_ev[atomicAdd(deferred, 1ull)] = e;  // left the tile: later, globally
+    ev[begin[p] + atomicAdd(&deferred_n[p], 1ull)] = e;  // left the tile: later, globally
+}
+
+// tile_region[t] = the region of every tile t (one CTA per region).
+__global__ void k_tile_map(TileAux aux, int parts, const uint32_t *use_binned) {
+  if (ld_volatile_u32(use_binned) == 0u) return;
+  const int p = blockIdx.x;
+  if (p >= parts) return;
+  const uint32_t t0 = aux.region_tile0[p], t1 = aux.region_tile0[p + 1];
+  for (uint32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) aux.tile_region[t] = (uint16_t)p;
 }
 
 // Persistent CTAs take tiles: a bulk copy brings the tile into shared memory
 // while the threads load their first events; the events are applied there;
 // a bulk copy writes the tile back while the CTA moves to its next tile.
+// Tiles are numbered compactly over the chain's regions; a tile's region
+// gives its table (the item's descriptor), its first slot and its bucket.
+// An event whose probe leaves its tile is listed in its region's part of the
+// first event buffer (which the split has consumed, and which holds at least
+// as many places as the region has events) for the global pass.
 //
-// FRESH: the table is being rebuilt from empty (dbg_build_reads), so its
-// contents are not read at all: every tile starts in shared memory as EMPTY
-// slots with zero counters and fingerprints, and every tile of the table --
-// with events or without -- is written back.  That one write is the table's
-// reset: the separate emptying pass (a full write of the table) disappears.
-// Each thread copies out and then re-initialises the same 16-byte words of
-// the tile, so the next tile needs no extra barrier.
+// FRESH: the tables are being rebuilt from empty (dbg_build_reads,
+// dbg_build_batch), so their contents are not read at all: every tile starts
+// in shared memory as EMPTY slots with zero counters and fingerprints, and
+// every tile -- with events or without -- is written back.  That one write
+// is the tables' reset: the separate emptying pass (a full write of every
+// table) disappears.  Each thread copies out and then re-initialises the
+// same 16-byte words of the tile, so the next tile needs no extra barrier.
 __device__ __forceinline__ void empty_tile_words(uint4 *st4, uint32_t *fp32) {
   const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);  // key EMPTY, cnt[0..1]
   const uint4 tail = make_uint4(0u, 0u, 0u, 0u);                    // cnt[2..3], pad
@@ -1034,12 +1099,11 @@ __device__ __forceinline__ void empty_tile_words(uint4 *st4, uint32_t *fp32) {
   for (int i = threadIdx.x; i < kFpBytes / 4; i += blockDim.x) fp32[i] = 0u;
 }
 
-template <int BLOCK, bool FRESH>
-__global__ void __launch_bounds__(BLOCK)
-    k_tile_apply(const uint64_t *__restrict__ ev2, uint64_t *deferred_ev, TileAux aux, int tpr,
-                 uint64_t n_tiles, Slot *table, uint64_t n_slots, uint32_t max_probes,
-                 uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
-                 unsigned long long *spill_count, const uint32_t *use_binned) {
+template <int BLOCK, bool FRESH, int N>
+__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 threads per SM
+    k_tile_apply(const __grid_constant__ ItemPack<N> pk, const uint64_t *__restrict__ ev2,
+                 uint64_t *ev, const unsigned long long *begin, TileAux aux, int parts,
+                 int tpr_log2, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   extern __shared__ __align__(16) unsigned char smem[];  // (bulk copies need 16 bytes)
   Slot *st = reinterpret_cast<Slot *>(smem);                 // kTileSlots slots
@@ -1057,15 +1121,22 @@ __global__ void __launch_bounds__(BLOCK)
   }
   __syncthreads();
   uint32_t parity = 0;
+  const uint64_t n_tiles = aux.region_tile0[parts];
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    // the tile's bucket: its events up to the bucket's size (the rest overflowed)
-    const uint64_t p = t / (uint64_t)tpr;
+    // the tile's region, table and bucket: its events up to the bucket's
+    // size (the rest overflowed).  One table's regions all hold 2^tpr_log2
+    // tiles but the last; a chain of many tables looks its tiles up.
+    const int p = N == 1 ? (int)(t >> tpr_log2) : (int)aux.tile_region[t];
+    const uint64_t j = t - aux.region_tile0[p];
+    // (one table: its fields stay kernel parameters, not registers)
+    const ItemDesc &it = pk.d[N == 1 ? 0 : aux.region_item[p]];
     const uint32_t cap = aux.tile_cap[p];
-    const uint64_t a = aux.region_base[p] + (t - p * (uint64_t)tpr) * cap;
+    const uint64_t a = aux.region_base[p] + j * cap;
     const uint64_t b = a + min(aux.fill[t], cap);
-    const uint64_t first = t << kTileLog2;
-    // a tile past the table's end (never has an event) is not there at all
-    if (first >= n_slots) continue;
+    const uint64_t first = aux.region_first[p] + (j << kTileLog2);
+    const uint64_t n_slots = it.n_slots;
+    Slot *table = it.table;
+    uint32_t *status = it.status;
     const int len = (int)min((uint64_t)kTileSlots, n_slots - first);
     uint64_t e[kBatch];
     if constexpr (FRESH) {
@@ -1097,10 +1168,10 @@ __global__ void __launch_bounds__(BLOCK)
         for (int wi = threadIdx.x; wi < kFpBytes / 4; wi += BLOCK) {
           uint32_t v = 0u;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int sl = 4 * wi + j;
+          for (int jj = 0; jj < 4; ++jj) {
+            const int sl = 4 * wi + jj;
             const unsigned long long k = sl < len ? st[sl].key : kEmpty;
-            if (k != kEmpty) v |= slot_fp(key_hash(k)) << (8 * j);
+            if (k != kEmpty) v |= slot_fp(key_hash(k)) << (8 * jj);
           }
           fp32[wi] = v;
         }
@@ -1126,8 +1197,8 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
         for (int r = 0; r < kBatch; ++r)
           if (e[r] != kEmpty)
-            tile_event(e[r], st, fp, first, len, n_slots, max_probes, status, spill, spill_cap,
-                       spill_count, deferred_ev, aux.deferred);
+            tile_event(e[r], st, fp, first, len, n_slots, it.max_probes, status, it.spill,
+                       it.spill_cap, it.spill_count, p, ev, begin, aux.deferred_n);
         base += (uint64_t)BLOCK * kBatch;
         if (base >= b) break;
         load_batch<BLOCK>(ev2, base, b, e);
@@ -1155,29 +1226,62 @@ __global__ void __launch_bounds__(BLOCK)
   if (!FRESH && threadIdx.x == 0) bulk_wait_all();
 }
 
-// The events that left their tile, then those of the overflow area, from
-// their home slots, with the global find-or-claim.
-__global__ void k_tile_deferred(const uint64_t *__restrict__ deferred_ev,
-                                const uint64_t *__restrict__ ev2, TileAux aux, int parts,
-                                Slot *table, uint64_t n_slots, uint32_t max_probes,
-                                uint32_t *status, SpillRecord *spill, uint64_t spill_cap,
-                                unsigned long long *spill_count, const uint32_t *use_binned) {
+// One event, from its home slot, with the global find-or-claim (its tile is
+// final by now).
+__device__ __forceinline__ void global_event(uint64_t e, const ItemDesc &it) {
+  const unsigned long long key = e >> 3;
+  uint64_t s;
+  if (find_or_claim(it.table, it.n_slots, it.max_probes, key, s)) {
+    if (e & 4ull) atomicAdd(&it.table[s].cnt[e & 3ull], 1u);
+  } else {
+    spill_or_fail(it.spill, it.spill_cap, it.spill_count, it.status, key, (e & 4ull) != 0,
+                  (uint32_t)(e & 3ull));
+  }
+}
+
+// The events that left their tile (each region's list), then those of the
+// overflow area ((event, region) pairs), from their home slots.
+template <int N>
+__global__ void k_tile_deferred(const __grid_constant__ ItemPack<N> pk,
+                                const uint64_t *__restrict__ ev,
+                                const uint64_t *__restrict__ ev2, const unsigned long long *begin,
+                                TileAux aux, int parts, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
-  const uint64_t nd = *aux.deferred;
-  const uint64_t n = nd + *aux.overflow;  // (all of it written: the flag is still set)
+  for (int p = blockIdx.x; p < parts; p += gridDim.x) {
+    const uint64_t n = aux.deferred_n[p];
+    if (n == 0) continue;
+    if (threadIdx.x == 0) atomicAdd(aux.deferred, (unsigned long long)n);
+    const ItemDesc &it = pk.d[aux.region_item[p]];
+    const uint64_t *list = ev + begin[p];
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) global_event(list[i], it);
+  }
+  const uint64_t no = *aux.overflow;  // (all of it written: the flag is still set)
   const uint64_t *over = ev2 + aux.region_base[parts];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint64_t e = i < nd ? deferred_ev[i] : over[i - nd];
-    const unsigned long long key = e >> 3;
-    uint64_t s;
-    if (find_or_claim(table, n_slots, max_probes, key, s)) {
-      if (e & 4ull) atomicAdd(&table[s].cnt[e & 3ull], 1u);
-    } else {
-      spill_or_fail(spill, spill_cap, spill_count, status, key, (e & 4ull) != 0,
-                    (uint32_t)(e & 3ull));
-    }
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < no; i += stride)
+    global_event(over[2 * i], pk.d[aux.region_item[over[2 * i + 1]]]);
+}
+
+// Empty every item's table (grid: x strides over the slots, y = item); with
+// a gate, nothing happens when *gate != 0 (the binned kernels did the work: a
+// rebuild's tiled apply has emptied the tables itself); without one, the
+// items' sticky statuses and spill counts are cleared too.
+template <int N>
+__global__ void k_tables_init(const __grid_constant__ ItemPack<N> pk, const uint32_t *gate) {
+  if (gate != nullptr && ld_volatile_u32(gate) != 0u) return;
+  const int i = blockIdx.y;
+  if (i >= pk.n_items) return;
+  if (gate == nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    *pk.d[i].status = 0u;
+    *pk.d[i].spill_count = 0ull;
   }
+  uint4 *t = reinterpret_cast<uint4 *>(pk.d[i].table);
+  const uint64_t n_vec = 2 * pk.d[i].n_slots;
+  const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
+  const uint4 tail = make_uint4(0u, 0u, 0u, 0u);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_vec; v += stride)
+    t[v] = (v & 1) ? tail : head;
 }
 
 int ceil_log2(uint64_t x) {
@@ -1204,49 +1308,74 @@ struct MetaView {
   unsigned long long *ctr;     // 4 counters; ctr[3] holds the use-binned flag
   uint32_t *flag;
   unsigned long long *apply_ctr;  // kBinApplyCounters
+  unsigned long long *totals;  // kBatchItems: vertex positions per item
   uint32_t *hist;              // kBinSlices * kBinMaxParts
 };
 
-MetaView meta_view(dbg_handle h) {
+MetaView meta_view(const BinScratch &sc) {
   MetaView v;
-  unsigned long long *b = h->bin_meta;
+  unsigned long long *b = sc.meta;
   v.begin = b;
   v.counts = v.begin + kBinMaxParts + 1;
   v.cursor = v.counts + kBinMaxParts;
   v.ctr = v.cursor + kBinMaxParts;
   v.flag = reinterpret_cast<uint32_t *>(v.ctr + 3);
   v.apply_ctr = v.ctr + 4;
-  v.hist = reinterpret_cast<uint32_t *>(v.apply_ctr + (size_t)kBinMaxParts * kBinApplyCounters);
+  v.totals = v.apply_ctr + (size_t)kBinMaxParts * kBinApplyCounters;
+  v.hist = reinterpret_cast<uint32_t *>(v.totals + kBatchItems);
   return v;
 }
 
-int ensure_bin_scratch(dbg_handle h, uint64_t events) {
-  if (events == 0)
-    events = std::max(kBinMinEvents, kBinEventsPerSlot * h->n_slots + h->n_slots / 4);
-  if (!h->bin_meta) {
+void free_bin_scratch(BinScratch &sc) {
+  cudaFree(sc.ev);
+  cudaFree(sc.ev2);
+  cudaFree(sc.aux);
+  cudaFree(sc.meta);
+  if (sc.done) cudaEventDestroy(sc.done);
+  sc = BinScratch{};
+}
+
+namespace {
+
+uint64_t default_events(uint64_t n_slots) {
+  return std::max(kBinMinEvents, kBinEventsPerSlot * n_slots + n_slots / 4);
+}
+
+// The meta area, the ordering event and an event buffer of exactly `events`
+// events (a buffer of another size is replaced, after the device is idle:
+// earlier calls may still read it).
+int ensure_events(BinScratch &sc, uint64_t events) {
+  if (!sc.meta) {
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, kBinMetaBytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(binned meta)");
-    h->bin_meta = static_cast<unsigned long long *>(p);
+    sc.meta = static_cast<unsigned long long *>(p);
   }
-  if (!h->bin_done) {
-    DBG_CK(cudaEventCreateWithFlags(&h->bin_done, cudaEventDisableTiming));
-  }
-  if (h->bin_cap != events) {
-    DBG_CK(cudaDeviceSynchronize());  // earlier binned calls may still read the old buffer
-    cudaFree(h->bin_ev);
-    cudaFree(h->bin_ev2);  // the tiled apply's buffer follows the event capacity
-    h->bin_ev = h->bin_ev2 = nullptr;
-    h->bin_cap = 0;
+  if (!sc.done) DBG_CK(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming));
+  if (sc.cap != events) {
+    DBG_CK(cudaDeviceSynchronize());
+    cudaFree(sc.ev);
+    cudaFree(sc.ev2);  // the tiled apply's buffer follows the event capacity
+    sc.ev = sc.ev2 = nullptr;
+    sc.cap = 0;
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, events * sizeof(uint64_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(binned events)");
-    h->bin_ev = static_cast<uint64_t *>(p);
-    h->bin_cap = events;
+    sc.ev = static_cast<uint64_t *>(p);
+    sc.cap = events;
   }
   return DBG_OK;
 }
 
+}  // namespace
+
+uint64_t bin_events_wanted(dbg_handle h) {
+  return h->bin_want ? h->bin_want : default_events(h->n_slots);
+}
+
+int ensure_bin_scratch(dbg_handle h, uint64_t events) {
+  return ensure_events(h->bin, events ? events : bin_events_wanted(h));
+}
 
 namespace {
 
@@ -1258,66 +1387,95 @@ uint64_t tile_unit(int tpr) { return std::max<uint64_t>(16384, 64ull * (uint64_t
 uint64_t ev2_capacity(uint64_t bin_cap) {
   return std::min<uint64_t>(bin_cap + bin_cap / 8 + (1ull << 20), 0xFFFFFFFFull);
 }
+// The largest first buffer whose second one stays within 32-bit positions.
+constexpr uint64_t kMaxChainEvents = 3800000000ull;
 
-// Layout of the tiled apply's aux buffer for a geometry.
+// Layout of the tiled apply's aux buffer for `parts` regions and `tiles`
+// tiles (compact numbering).
 struct TileAuxLayout {
-  size_t unit_base, region_base, tile_cap, fill, counters, total;
+  size_t unit_base, region_base, tile_cap, fill, item, first, nslots, tile0, map, deferred_n,
+      counters, total;
 };
 
-TileAuxLayout tile_aux_layout(const BinGeometry &geo, int tpr) {
+TileAuxLayout tile_aux_layout(int parts, uint64_t tiles) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t P = (size_t)parts;
   TileAuxLayout l;
   l.unit_base = 0;
-  l.region_base = al(l.unit_base + ((size_t)geo.parts + 1) * 8);
-  l.tile_cap = al(l.region_base + ((size_t)geo.parts + 1) * 8);
-  l.fill = al(l.tile_cap + (size_t)geo.parts * 4);
-  l.counters = al(l.fill + (size_t)geo.parts * tpr * 4);
+  l.region_base = al(l.unit_base + (P + 1) * 8);
+  l.tile_cap = al(l.region_base + (P + 1) * 8);
+  l.fill = al(l.tile_cap + P * 4);
+  l.item = al(l.fill + (size_t)tiles * 4);
+  l.first = al(l.item + P * 4);
+  l.nslots = al(l.first + P * 8);
+  l.tile0 = al(l.nslots + P * 8);
+  l.map = al(l.tile0 + (P + 1) * 4);
+  l.deferred_n = al(l.map + (size_t)tiles * 2);
+  l.counters = al(l.deferred_n + P * 8);
   l.total = al(l.counters + 16);
   return l;
 }
 
-TileAux tile_aux(dbg_handle h, const BinGeometry &geo, int tpr) {
-  const TileAuxLayout l = tile_aux_layout(geo, tpr);
-  char *b = static_cast<char *>(h->bin_aux);
+TileAux tile_aux(const BinScratch &sc, int parts, uint64_t tiles) {
+  const TileAuxLayout l = tile_aux_layout(parts, tiles);
+  char *b = static_cast<char *>(sc.aux);
   TileAux a;
   a.unit_base = reinterpret_cast<unsigned long long *>(b + l.unit_base);
   a.region_base = reinterpret_cast<unsigned long long *>(b + l.region_base);
   a.tile_cap = reinterpret_cast<uint32_t *>(b + l.tile_cap);
   a.fill = reinterpret_cast<uint32_t *>(b + l.fill);
+  a.region_item = reinterpret_cast<uint32_t *>(b + l.item);
+  a.region_first = reinterpret_cast<unsigned long long *>(b + l.first);
+  a.region_nslots = reinterpret_cast<unsigned long long *>(b + l.nslots);
+  a.region_tile0 = reinterpret_cast<uint32_t *>(b + l.tile0);
+  a.tile_region = reinterpret_cast<uint16_t *>(b + l.map);
+  a.deferred_n = reinterpret_cast<unsigned long long *>(b + l.deferred_n);
   a.overflow = reinterpret_cast<unsigned long long *>(b + l.counters);
   a.deferred = a.overflow + 1;
   return a;
 }
 
-// The second event buffer and the aux buffer of the tiled apply; false (and
-// the streaming apply is used) if they cannot be had -- out of memory, or
-// inside a stream capture that began before they existed.
-bool ensure_tile_scratch(dbg_handle h, const BinGeometry &geo, int tpr, bool capturing) {
-  const size_t need = tile_aux_layout(geo, tpr).total;
-  if (h->bin_ev2 && h->bin_aux && h->bin_aux_bytes >= need) return true;
+// The second event buffer and the aux buffer of the tiled apply; false if
+// they cannot be had -- out of memory, or inside a stream capture that began
+// before they existed.
+bool ensure_tile_scratch(BinScratch &sc, int parts, uint64_t tiles, bool capturing) {
+  const size_t need = tile_aux_layout(parts, tiles).total;
+  if (sc.ev2 && sc.aux && sc.aux_bytes >= need) return true;
   if (capturing) return false;
   if (cudaDeviceSynchronize() != cudaSuccess) return false;  // earlier calls may use them
-  if (!h->bin_ev2) {
+  if (!sc.ev2) {
     void *p = nullptr;
-    if (cudaMalloc(&p, ev2_capacity(h->bin_cap) * sizeof(uint64_t)) != cudaSuccess) {
+    if (cudaMalloc(&p, ev2_capacity(sc.cap) * sizeof(uint64_t)) != cudaSuccess) {
       cudaGetLastError();  // clear the allocation failure
       return false;
     }
-    h->bin_ev2 = static_cast<uint64_t *>(p);
+    sc.ev2 = static_cast<uint64_t *>(p);
   }
-  if (h->bin_aux_bytes < need) {
-    cudaFree(h->bin_aux);
-    h->bin_aux = nullptr;
-    h->bin_aux_bytes = 0;
+  if (sc.aux_bytes < need) {
+    cudaFree(sc.aux);
+    sc.aux = nullptr;
+    sc.aux_bytes = 0;
     void *p = nullptr;
     if (cudaMalloc(&p, need) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
-    h->bin_aux = p;
-    h->bin_aux_bytes = need;
+    sc.aux = p;
+    sc.aux_bytes = need;
   }
   return true;
+}
+
+// Tiles (compact numbering) of a table of n_slots slots cut into regions of
+// 2^shift slots.
+uint64_t table_tiles(uint64_t n_slots, int shift) {
+  const uint64_t R = 1ull << shift;
+  const uint64_t full = n_slots >> shift, rest = n_slots & (R - 1);
+  return full * (R >> kTileLog2) + ((rest + kTileSlots - 1) >> kTileLog2);
+}
+
+int regions_of(uint64_t n_slots, int shift) {
+  return (int)((n_slots + (1ull << shift) - 1) >> shift);
 }
 
 }  // namespace
@@ -1337,7 +1495,7 @@ int launch_apply(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int s
   for (int gi = 0; gi < n_groups; ++gi) {
     const int p0 = gi * group, p1 = std::min(geo.parts, p0 + group);
     k_bin_apply<B, U, M><<<grid, B, 0, s>>>(
-        h->bin_ev, mv.begin, p0, p1, mv.flag, h->table, h->n_slots, h->max_probes, h->d_status,
+        h->bin.ev, mv.begin, p0, p1, mv.flag, h->table, h->n_slots, h->max_probes, h->d_status,
         mv.apply_ctr + (size_t)gi * t.apply_counters, t.apply_counters, h->d_spill, h->spill_cap,
         h->d_spill_count);
   }
@@ -1356,8 +1514,8 @@ int launch_apply_m(dbg_handle h, const MetaView &mv, const BinGeometry &geo, int
 }
 
 template <int BT, bool STAGED>
-int launch_tile_scatter(dbg_handle h, const MetaView &mv, const TileAux &aux,
-                        const BinGeometry &geo, uint64_t unit, int tpr, int sms, cudaStream_t s) {
+int launch_tile_scatter(const BinScratch &sc, const MetaView &mv, const TileAux &aux, int parts,
+                        uint64_t unit, int tpr, int sms, cudaStream_t s, uint32_t *status) {
   if (tpr > kMaxBinsPerThread * BT) return DBG_ERR_INVALID_ARG;  // (the launch sizes BT by tpr)
   const size_t smem = tile_scatter_smem<BT, STAGED>(tpr);
   // (set even below 48 KB: the kernel's static shared memory counts too)
@@ -1367,11 +1525,141 @@ int launch_tile_scatter(dbg_handle h, const MetaView &mv, const TileAux &aux,
   DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_scatter<BT, STAGED>, BT,
                                                        smem));
   k_tile_scatter<BT, STAGED><<<std::max(1, per_sm) * sms, BT, smem, s>>>(
-      h->bin_ev, h->bin_ev2, ev2_capacity(h->bin_cap), mv.begin, mv.counts, aux, geo.parts, unit,
-      geo.shift, tpr, h->n_slots, h->d_status, mv.flag);
+      sc.ev, sc.ev2, ev2_capacity(sc.cap), mv.begin, mv.counts, aux, parts, unit, tpr, status,
+      mv.flag);
   DBG_CK(cudaGetLastError());
   return DBG_OK;
 }
+
+namespace {
+
+// Records the kernel timer's marks of a single-table call (no-op for batches).
+struct Marks {
+  dbg_handle h = nullptr;
+  int call = -1;
+  void operator()(int m, cudaStream_t s) const {
+    if (h) timer_mark(h, call, m, s);
+  }
+};
+
+// One tiled chain over items[0..n) (N >= n): their tables are cut into
+// regions of 2^shift slots (`parts` of them, `tiles` tiles), item i's first
+// region is items[i].region0, and items[i].tile_begin numbers the walk's
+// tiles of kScatterTileReads reads.  `direct` holds the same items numbered
+// for the direct kernel (`direct_tiles` tiles), which does the call instead
+// when the events do not fit the scratch.  The scratch's event buffer, second
+// buffer and aux area must exist.  `status` receives a timeout of the split.
+template <int N>
+int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int parts,
+                uint64_t tiles, uint64_t walk_tiles, const ItemDesc *direct,
+                uint64_t direct_tiles, const dbg_tuning &tuning, int sms, cudaStream_t s,
+                bool fresh, const Marks &mark) {
+  const int scatter_reads = scatter_tile_reads(tuning);
+  const MetaView mv = meta_view(sc);
+  const int tpr = 1 << (shift - kTileLog2);
+  const TileAux aux = tile_aux(sc, parts, tiles);
+  ItemPack<N> pk{};
+  pk.n_items = n;
+  pk.total_tiles = walk_tiles;
+  for (int i = 0; i < n; ++i) pk.d[i] = items[i];
+  const uint64_t slices = std::min<uint64_t>(walk_tiles, kBinSlices);
+  DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
+  DBG_CK(cudaMemsetAsync(mv.counts, 0, parts * sizeof(unsigned long long), s));
+  DBG_CK(cudaMemsetAsync(mv.totals, 0, n * sizeof(unsigned long long), s));
+  DBG_CK(cudaMemsetAsync(aux.fill, 0, tiles * sizeof(uint32_t), s));
+  sc.counters = aux.overflow;
+  mark(1, s);
+  // bucket sizing: positions per item, then buckets and the region table
+  {
+    const int gx = std::max(1, (sms * 4 + n - 1) / n);
+    k_bin_totals<N><<<dim3(gx, n), 256, 0, s>>>(pk, mv.totals, fresh ? 1 : 0);
+    DBG_CK(cudaGetLastError());
+    k_bin_buckets<N><<<1, 1024, 0, s>>>(pk, mv.totals, shift, parts, mv.begin, mv.cursor, sc.cap,
+                                        mv.ctr, mv.flag, aux);
+    DBG_CK(cudaGetLastError());
+    if (N > 1) {
+      k_tile_map<<<parts, 256, 0, s>>>(aux, parts, mv.flag);
+      DBG_CK(cudaGetLastError());
+    }
+  }
+  mark(3, s);
+  {
+    // 512 threads: flushes of 4096 events, so that a region's run in a flush
+    // is long enough to fill whole sectors (shorter runs cost the L2 a
+    // read-modify-write of partly written sectors)
+    constexpr int BS = 512;
+    const size_t smem = scatter_smem<BS>(scatter_reads, parts);
+    DBG_CK(cudaFuncSetAttribute(k_bin_scatter<BS, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+    int per_sm = 0;
+    DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<BS, N>, BS, smem));
+    const int grid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>(slices, (uint64_t)std::max(1, per_sm) * sms));
+    k_bin_scatter<BS, N><<<grid, BS, smem, s>>>(pk, scatter_reads, shift, parts, slices,
+                                                mv.hist, mv.cursor, sc.ev, sc.cap, mv.ctr, mv.flag,
+                                                mv.begin + 1);
+    DBG_CK(cudaGetLastError());
+  }
+  const uint64_t unit = tile_unit(tpr);
+  mark(4, s);
+  k_tile_units<<<1, 1024, 0, s>>>(mv.counts, mv.begin, mv.cursor, parts, unit,
+                                  ev2_capacity(sc.cap), aux, mv.flag);
+  DBG_CK(cudaGetLastError());
+  // chunks of 8 events per thread: larger blocks for more tiles per region,
+  // so that each tile's run in a chunk stays several events long (a timeout of
+  // the staged copies is recorded in the first item's status)
+  // (tuning.split_threads overrides the choice when it has at most four bins
+  // a thread)
+  int bt = tpr <= 256 ? 256 : tpr <= 1024 ? 512 : 1024;
+  if (tuning.split_threads > 0 && tpr <= kMaxBinsPerThread * tuning.split_threads)
+    bt = tuning.split_threads;
+  if (bt == 256) {
+    DBG_TRY((launch_tile_scatter<256, true>(sc, mv, aux, parts, unit, tpr, sms, s,
+                                            items[0].status)));
+  } else if (bt == 512) {  // (1024 tiles: two bins per thread; measured faster than 1024 threads)
+    DBG_TRY((launch_tile_scatter<512, true>(sc, mv, aux, parts, unit, tpr, sms, s,
+                                            items[0].status)));
+  } else {
+    DBG_TRY((launch_tile_scatter<1024, false>(sc, mv, aux, parts, unit, tpr, sms, s,
+                                              items[0].status)));
+  }
+  mark(5, s);
+  {
+    // 512 threads: three such CTAs (66 KB of shared memory each: the tile
+    // and its fingerprints) fill an SM with 48 warps, enough to hide the
+    // dependent hash and probe latencies
+    constexpr int BA = 512;
+    constexpr size_t smem = (size_t)kTileSlots * sizeof(Slot) + kFpBytes;
+    auto kern = fresh ? k_tile_apply<BA, true, N> : k_tile_apply<BA, false, N>;
+    DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BA, smem));
+    const uint64_t grid = std::max<uint64_t>(
+        1, std::min<uint64_t>(tiles, (uint64_t)std::max(1, per_sm) * sms));
+    kern<<<(int)grid, BA, smem, s>>>(pk, sc.ev2, sc.ev, mv.begin, aux, parts, shift - kTileLog2,
+                                     mv.flag);
+    DBG_CK(cudaGetLastError());
+  }
+  mark(6, s);
+  k_tile_deferred<N><<<sms * 4, 256, 0, s>>>(pk, sc.ev, sc.ev2, mv.begin, aux, parts, mv.flag);
+  DBG_CK(cudaGetLastError());
+  // the direct insert runs only if the events did not fit the buffer (then no
+  // binned kernel touched the tables: a rebuild from empty empties them first)
+  mark(7, s);
+  if (fresh) {
+    ItemPack<N> ip{};
+    ip.n_items = n;
+    for (int i = 0; i < n; ++i) ip.d[i] = items[i];
+    k_tables_init<N><<<dim3(std::max(1, sms * 8 / n), n), 256, 0, s>>>(ip, mv.flag);
+    DBG_CK(cudaGetLastError());
+  }
+  const int st = launch_insert(direct, n, direct_tiles, tuning, sms, s, mv.flag);
+  if (st != DBG_OK) return st;
+  mark(8, s);
+  return DBG_OK;
+}
+
+}  // namespace
 
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
                   cudaStream_t s, int call, bool fresh) {
@@ -1379,13 +1667,13 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   const dbg_tuning t = resolve_tuning(tuning);
   // the tiled apply re-partitions each region by tile, so its first pass can
   // use coarser regions (fewer of them: a cheaper scatter); measured best at
-  // 1024 tiles per region on the 100 Mbp workload (512: 50.1 ms, 1024: 49.5 ms,
-  // 256: 53.3 ms)
-  const bool want_tiled = t.apply_mode != 1 && h->bin_cap < (1ull << 32);
+  // 1024 tiles per region on the 100 Mbp workload (2^20-slot regions:
+  // 47.6 ms a build, 2^21: 46.9 ms, 2^22: 51.3 ms)
+  const bool want_tiled = t.apply_mode != 1 && h->bin.cap < kMaxChainEvents;
   const BinGeometry geo =
       bin_geometry(h->n_slots, t.region_log2 > 0 ? t.region_log2 : (want_tiled ? kTiledShift : 0));
-  const MetaView mv = meta_view(h);
   const int sms = std::max(1, h->sm_count);
+  const Marks mark{h, call};
 
   // binned calls on one handle share its scratch: order them.  Inside a
   // stream capture the captured calls are ordered by the stream itself, and
@@ -1393,41 +1681,45 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
   DBG_CK(cudaStreamIsCapturing(s, &capture));
   const bool capturing = capture != cudaStreamCaptureStatusNone;
-  if (!capturing) DBG_CK(cudaStreamWaitEvent(s, h->bin_done, 0));
+  if (!capturing) DBG_CK(cudaStreamWaitEvent(s, h->bin.done, 0));
   const int tpr = 1 << std::max(0, geo.shift - kTileLog2);
+  const uint64_t n_tiles = table_tiles(h->n_slots, std::max(geo.shift, kTileLog2));
   // (bucket positions are kept in 32 bits: the event buffer must stay below
   // 2^32 events)
   const bool tiled = want_tiled && geo.shift >= kTileLog2 && tpr <= kMaxTilesPerRegion &&
-                     ensure_tile_scratch(h, geo, tpr, capturing);
-  // the read walk's own tiles ('tiles' counts the direct kernel's): the count
-  // pass and the scatter must walk the same ones; without a count pass the
-  // scatter takes larger tiles (fewer per-tile setups)
-  const int tile_reads = tiled ? kScatterTileReads : std::min(t.tile_reads, B);
+                     ensure_tile_scratch(h->bin, geo.parts, n_tiles, capturing);
+  h->bin.counters = nullptr;
+  if (tiled) {
+    ItemDesc walk = it;  // the scatter's read tiles (larger than the direct kernel's)
+    walk.tile_begin = 0;
+    walk.region0 = 0;
+    const uint64_t sr = (uint64_t)scatter_tile_reads(tuning);
+    const uint64_t walk_tiles = (it.n_reads + sr - 1) / sr;
+    ItemDesc direct = it;
+    direct.tile_begin = 0;
+    DBG_TRY(tiled_chain<1>(h->bin, &walk, 1, geo.shift, geo.parts, n_tiles, walk_tiles, &direct,
+                           tiles, tuning, sms, s, fresh, mark));
+    if (!capturing) DBG_CK(cudaEventRecord(h->bin.done, s));
+    return DBG_OK;
+  }
+
+  // the streaming apply: an exact count pass and its scan, the scatter into
+  // gap-free region ranges, then the apply (a rebuild empties the table
+  // first: this apply reads it)
+  if (fresh) DBG_TRY(launch_table_init(h->table, h->n_slots, s));
+  const MetaView mv = meta_view(h->bin);
+  const int tile_reads = std::min(t.tile_reads, B);
   const uint64_t walk_tiles = (it.n_reads + (uint64_t)tile_reads - 1) / (uint64_t)tile_reads;
   const uint64_t slices = std::min<uint64_t>(walk_tiles, kBinSlices);
   ItemPack<1> pk{};
   pk.n_items = 1;
   pk.total_tiles = walk_tiles;
   pk.d[0] = it;
-  // a rebuild from empty folds the reset into the tiled apply; the other
-  // applies read the table, so it is emptied first
-  if (fresh && !tiled) DBG_TRY(launch_table_init(h->table, h->n_slots, s));
+  pk.d[0].region0 = 0;
   DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, geo.parts * sizeof(unsigned long long), s));
-  h->bin_counters = nullptr;
-  if (tiled) {  // the tile buckets' fill counts
-    const TileAux aux = tile_aux(h, geo, tpr);
-    DBG_CK(cudaMemsetAsync(aux.fill, 0, (size_t)geo.parts * tpr * 4, s));
-    h->bin_counters = aux.overflow;
-  }
-  timer_mark(h, call, 1, s);
-  if (tiled) {  // buckets instead of the count pass and its scan
-    k_bin_total<<<sms * 4, 256, 0, s>>>(it.offsets, it.n_reads, it.k, mv.ctr + 2);
-    DBG_CK(cudaGetLastError());
-    k_bin_buckets<<<1, 1024, 0, s>>>(mv.ctr + 2, h->n_slots, geo.shift, geo.parts, mv.begin,
-                                     mv.cursor, h->bin_cap, mv.ctr, mv.flag);
-    DBG_CK(cudaGetLastError());
-  } else {
+  mark(1, s);
+  {
     const size_t smem = tile_smem_bytes(tile_reads) + (size_t)geo.parts * 4;
     if (smem > 48 * 1024)
       DBG_CK(cudaFuncSetAttribute(k_bin_count<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1437,95 +1729,178 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     k_bin_count<B><<<grid, B, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices, mv.hist,
                                          mv.counts, mv.ctr);
     DBG_CK(cudaGetLastError());
-    timer_mark(h, call, 2, s);
-    k_bin_scan<<<1, 1024, 0, s>>>(mv.counts, geo.parts, mv.begin, mv.cursor, h->bin_cap, mv.ctr,
+    mark(2, s);
+    k_bin_scan<<<1, 1024, 0, s>>>(mv.counts, geo.parts, mv.begin, mv.cursor, h->bin.cap, mv.ctr,
                                   mv.flag);
     DBG_CK(cudaGetLastError());
   }
-  timer_mark(h, call, 3, s);
+  mark(3, s);
   {
-    // 512 threads: flushes of 4096 events, so that a region's run in a flush
-    // is long enough to fill whole sectors (shorter runs cost the L2 a
-    // read-modify-write of partly written sectors)
     constexpr int BS = 512;
     const size_t smem = scatter_smem<BS>(tile_reads, geo.parts);
-    DBG_CK(cudaFuncSetAttribute(k_bin_scatter<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DBG_CK(cudaFuncSetAttribute(k_bin_scatter<BS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
     int per_sm = 0;
-    DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<BS>, BS, smem));
+    DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<BS, 1>, BS, smem));
     const int grid = (int)std::min<uint64_t>(slices, (uint64_t)std::max(1, per_sm) * sms);
-    k_bin_scatter<BS><<<grid, BS, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices, mv.hist,
-                                             mv.cursor, h->bin_ev, h->bin_cap, mv.ctr, mv.flag,
-                                             tiled ? mv.begin + 1 : nullptr);
+    k_bin_scatter<BS, 1><<<grid, BS, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices,
+                                                mv.hist, mv.cursor, h->bin.ev, h->bin.cap, mv.ctr,
+                                                mv.flag, nullptr);
     DBG_CK(cudaGetLastError());
   }
-  if (tiled) {
-    const uint64_t unit = tile_unit(tpr);
-    const TileAux aux = tile_aux(h, geo, tpr);
-    const uint64_t n_tiles = (uint64_t)geo.parts * tpr;
-    timer_mark(h, call, 4, s);
-    k_tile_units<<<1, 1024, 0, s>>>(mv.counts, mv.begin, mv.cursor, geo.parts, geo.shift, tpr,
-                                    h->n_slots, unit, ev2_capacity(h->bin_cap), aux, mv.flag);
-    DBG_CK(cudaGetLastError());
-    // chunks of 8 events per thread: larger blocks for more tiles per region,
-    // so that each tile's run in a chunk stays several events long
-    if (tpr <= 256) {
-      DBG_TRY((launch_tile_scatter<256, true>(h, mv, aux, geo, unit, tpr, sms, s)));
-    } else if (tpr <= 1024) {  // (1024 tiles: two bins per thread; measured faster than 1024 threads)
-      DBG_TRY((launch_tile_scatter<512, true>(h, mv, aux, geo, unit, tpr, sms, s)));
-    } else {
-      DBG_TRY((launch_tile_scatter<1024, false>(h, mv, aux, geo, unit, tpr, sms, s)));
-    }
-    timer_mark(h, call, 5, s);
-    {
-      // 512 threads: three such CTAs (66 KB of shared memory each: the tile
-      // and its fingerprints) fill an SM with 48 warps, enough to hide the
-      // dependent hash and probe latencies
-      constexpr int BA = 512;
-      constexpr size_t smem = (size_t)kTileSlots * sizeof(Slot) + kFpBytes;
-      auto kern = fresh ? k_tile_apply<BA, true> : k_tile_apply<BA, false>;
-      DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      int per_sm = 0;
-      DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BA, smem));
-      const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)std::max(1, per_sm) * sms);
-      kern<<<(int)grid, BA, smem, s>>>(h->bin_ev2, h->bin_ev, aux, tpr, n_tiles, h->table,
-                                       h->n_slots, h->max_probes, h->d_status, h->d_spill,
-                                       h->spill_cap, h->d_spill_count, mv.flag);
-      DBG_CK(cudaGetLastError());
-    }
-    timer_mark(h, call, 6, s);
-    k_tile_deferred<<<sms * 4, 256, 0, s>>>(h->bin_ev, h->bin_ev2, aux, geo.parts, h->table,
-                                            h->n_slots, h->max_probes, h->d_status, h->d_spill,
-                                            h->spill_cap, h->d_spill_count, mv.flag);
-    DBG_CK(cudaGetLastError());
-  } else {
-    timer_mark(h, call, 5, s);
-    switch (t.apply_unroll) {
-      case 2: DBG_TRY(launch_apply_m<B, 2>(h, mv, geo, sms, t, s)); break;
-      case 8: DBG_TRY(launch_apply_m<B, 8>(h, mv, geo, sms, t, s)); break;
-      default: DBG_TRY(launch_apply_m<B, 4>(h, mv, geo, sms, t, s)); break;
-    }
+  mark(5, s);
+  switch (t.apply_unroll) {
+    case 2: DBG_TRY((launch_apply_m<B, 2>(h, mv, geo, sms, t, s))); break;
+    case 8: DBG_TRY((launch_apply_m<B, 8>(h, mv, geo, sms, t, s))); break;
+    default: DBG_TRY((launch_apply_m<B, 4>(h, mv, geo, sms, t, s))); break;
   }
-  // the direct insert runs only if the events did not fit the buffer (then no
-  // binned kernel touched the table: a rebuild from empty empties it first)
-  timer_mark(h, call, 7, s);
-  if (fresh && tiled) DBG_TRY(launch_table_init(h->table, h->n_slots, s, mv.flag));
+  // the direct insert runs only if the events did not fit the buffer
+  mark(7, s);
   const int st = launch_insert(&it, 1, tiles, tuning, h->sm_count, s, mv.flag);
   if (st != DBG_OK) return st;
-  timer_mark(h, call, 8, s);
-  if (!capturing) DBG_CK(cudaEventRecord(h->bin_done, s));
+  mark(8, s);
+  if (!capturing) DBG_CK(cudaEventRecord(h->bin.done, s));
+  return DBG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches: chains of many tables, with the library's own scratch
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_batch_mu;
+BinScratch g_batch[kMaxDevices];
+
+}  // namespace
+
+int launch_tables_init(const ItemDesc *items, int n, int sm_count, cudaStream_t s) {
+  if (n <= 0) return DBG_OK;
+  if (n > kBatchItems) return DBG_ERR_INVALID_ARG;
+  ItemPack<kBatchItems> ip{};
+  ip.n_items = n;
+  for (int i = 0; i < n; ++i) ip.d[i] = items[i];
+  k_tables_init<kBatchItems><<<dim3(std::max(1, std::max(1, sm_count) * 8 / n), n), 256, 0, s>>>(
+      ip, nullptr);
+  DBG_CK(cudaGetLastError());
+  return DBG_OK;
+}
+
+int launch_binned_batch(const ItemDesc *items, const uint64_t *want, int n,
+                        const dbg_tuning &tuning, int sm_count, cudaStream_t s, bool fresh) {
+  if (n <= 0) return DBG_OK;
+  const dbg_tuning t = resolve_tuning(tuning);
+  const int shift = t.region_log2 > 0 ? std::max(t.region_log2, kTileLog2) : kTiledShift;
+  const int sms = std::max(1, sm_count);
+  int dev = 0;
+  DBG_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return DBG_ERR_INVALID_ARG;
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  DBG_CK(cudaStreamIsCapturing(s, &capture));
+  const bool capturing = capture != cudaStreamCaptureStatusNone;
+
+  // cut the items into chains: at most kBatchItems items, kBinMaxParts
+  // regions and kMaxChainEvents events each
+  struct Chain {
+    int i0, i1, parts;
+    uint64_t tiles, events;
+  };
+  std::vector<Chain> chains;
+  for (int i = 0; i < n;) {
+    Chain c{i, i, 0, 0, 0};
+    while (c.i1 < n) {
+      const int r = regions_of(items[c.i1].n_slots, shift);
+      const uint64_t ev = want[c.i1];
+      if (c.i1 > c.i0 && (c.i1 - c.i0 == kBatchItems || c.parts + r > kBinMaxParts ||
+                          c.events + ev > kMaxChainEvents))
+        break;
+      c.parts += r;
+      c.tiles += table_tiles(items[c.i1].n_slots, shift);
+      c.events += ev;
+      ++c.i1;
+    }
+    if (c.parts > kBinMaxParts) return DBG_ERR_INVALID_ARG;  // one table of too many regions
+    chains.push_back(c);
+    i = c.i1;
+  }
+  uint64_t need_events = 0, need_tiles = 0;
+  int need_parts = 0;
+  for (const Chain &c : chains) {
+    need_events = std::max(need_events, std::min(c.events, kMaxChainEvents));
+    need_tiles = std::max(need_tiles, c.tiles);
+    need_parts = std::max(need_parts, c.parts);
+  }
+
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BinScratch &sc = g_batch[dev];
+  bool ready = sc.meta && sc.done && sc.cap >= need_events &&
+               ensure_tile_scratch(sc, need_parts, need_tiles, true);
+  if (!ready && !capturing) {
+    DBG_TRY(ensure_events(sc, std::max(need_events, sc.cap)));
+    ready = ensure_tile_scratch(sc, need_parts, need_tiles, false);
+  }
+  if (!capturing) DBG_CK(cudaStreamWaitEvent(s, sc.done, 0));
+  const uint64_t sr = (uint64_t)scatter_tile_reads(tuning);
+  for (const Chain &c : chains) {
+    const int m = c.i1 - c.i0;
+    std::vector<ItemDesc> walk(items + c.i0, items + c.i1), direct(items + c.i0, items + c.i1);
+    uint64_t walk_tiles = 0, direct_tiles = 0;
+    int region0 = 0;
+    for (int i = 0; i < m; ++i) {
+      walk[i].tile_begin = walk_tiles;
+      walk[i].region0 = region0;
+      walk_tiles += (walk[i].n_reads + sr - 1) / sr;
+      region0 += regions_of(walk[i].n_slots, shift);
+      direct[i].tile_begin = direct_tiles;
+      direct_tiles += (direct[i].n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
+    }
+    if (!ready) {  // no scratch inside this capture: the direct insert does it
+      if (fresh) DBG_TRY(launch_tables_init(direct.data(), m, sms, s));
+      DBG_TRY(launch_insert(direct.data(), m, direct_tiles, tuning, sms, s));
+      continue;
+    }
+    DBG_TRY(tiled_chain<kBatchItems>(sc, walk.data(), m, shift, c.parts, c.tiles, walk_tiles,
+                                     direct.data(), direct_tiles, tuning, sms, s, fresh, Marks{}));
+  }
+  if (!capturing) DBG_CK(cudaEventRecord(sc.done, s));
+  return DBG_OK;
+}
+
+uint64_t batch_scratch_bytes(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return 0;
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  const BinScratch &sc = g_batch[dev];
+  uint64_t b = sc.aux_bytes + (sc.meta ? kBinMetaBytes : 0);
+  if (sc.ev) b += sc.cap * sizeof(uint64_t);
+  if (sc.ev2) b += ev2_capacity(sc.cap) * sizeof(uint64_t);
+  return b;
+}
+
+int release_batch_scratch() {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  int prev = 0;
+  DBG_CK(cudaGetDevice(&prev));
+  for (int d = 0; d < kMaxDevices; ++d) {
+    if (!g_batch[d].meta && !g_batch[d].ev) continue;
+    DBG_CK(cudaSetDevice(d));
+    DBG_CK(cudaDeviceSynchronize());
+    free_bin_scratch(g_batch[d]);
+  }
+  DBG_CK(cudaSetDevice(prev));
   return DBG_OK;
 }
 
 int binned_counters(dbg_handle h, uint64_t *out) {
   out[0] = out[1] = out[2] = 0;
-  if (!h->bin_meta) return DBG_OK;  // no binned call yet
+  if (!h->bin.meta) return DBG_OK;  // no binned call yet
   DBG_CK(cudaDeviceSynchronize());
   uint32_t flag = 0;
-  DBG_CK(cudaMemcpy(&flag, meta_view(h).flag, sizeof(flag), cudaMemcpyDeviceToHost));
+  DBG_CK(cudaMemcpy(&flag, meta_view(h->bin).flag, sizeof(flag), cudaMemcpyDeviceToHost));
   out[0] = flag != 0u;
-  if (flag && h->bin_counters) {
+  if (flag && h->bin.counters) {
     unsigned long long c[2] = {0ull, 0ull};  // overflow, deferred
-    DBG_CK(cudaMemcpy(c, h->bin_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    DBG_CK(cudaMemcpy(c, h->bin.counters, sizeof(c), cudaMemcpyDeviceToHost));
     out[1] = c[1];
     out[2] = c[0];
   }

@@ -1,11 +1,11 @@
-// Binned insert (see dbg_binned.cu): geometry and the host entry.
+// Binned insert (see dbg_binned.cu): geometry and the host entries.
 #pragma once
 
 #include "dbg_internal.cuh"
 
 namespace dbg {
 
-constexpr int kBinMaxParts = 2048;           // regions of the table, at most
+constexpr int kBinMaxParts = 2048;           // regions of one chain (one or many tables), at most
 constexpr uint64_t kBinMinTableBytes = 256ull << 20;  // auto mode: tables at least this big
 constexpr uint64_t kBinMinEvents = 16ull << 20;       // smallest event buffer
 constexpr uint64_t kBinEventsPerSlot = 4;             // default event buffer: 4.25 events per slot
@@ -18,10 +18,11 @@ constexpr int kBinApplyCounters = 64;                // apply: chunk counters pe
 
 // meta area: begin[kBinMaxParts + 1] | counts[kBinMaxParts] | cursor[kBinMaxParts] |
 // counters[4] (the last holds the flag) | apply counters[kBinMaxParts][kBinApplyCounters] |
-// slice histograms u32[kBinSlices][kBinMaxParts]
+// item totals[kBatchItems] | slice histograms u32[kBinSlices][kBinMaxParts]
 constexpr size_t kBinMetaBytes =
     ((size_t)kBinMaxParts + 1) * 8 + 2 * (size_t)kBinMaxParts * 8 + 4 * 8 +
-    (size_t)kBinMaxParts * kBinApplyCounters * 8 + (size_t)kBinSlices * kBinMaxParts * 4;
+    (size_t)kBinMaxParts * kBinApplyCounters * 8 + (size_t)kBatchItems * 8 +
+    (size_t)kBinSlices * kBinMaxParts * 4;
 
 struct BinGeometry {
   int shift;  // region = slots [p << shift, (p + 1) << shift)
@@ -32,8 +33,12 @@ struct BinGeometry {
 // most kBinMaxParts of them.
 BinGeometry bin_geometry(uint64_t n_slots, int region_log2);
 
+// The event capacity a handle's binned inserts use: what dbg_reserve_events
+// asked for, else the default of 4.25 per table slot.
+uint64_t bin_events_wanted(dbg_handle h);
+
 // Make sure the handle holds an event buffer of at least `events` events
-// (0: the default size) and the meta area.
+// (0: bin_events_wanted) and the meta area.
 int ensure_bin_scratch(dbg_handle h, uint64_t events);
 
 // Insert one read set through count / scan / scatter / apply, falling back to
@@ -44,6 +49,26 @@ int ensure_bin_scratch(dbg_handle h, uint64_t events);
 // instead of reading it, which empties the table without a pass of its own.
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
                   cudaStream_t s, int call, bool fresh = false);
+
+// Insert many read sets, each into its own table (k <= 31), through binned
+// chains: every chain is one launch of each binned kernel over all of its
+// items (up to kBatchItems of them and kBinMaxParts regions).  items[i]
+// carries the direct kernel's tile numbering (tile_begin over `tile_reads`
+// reads per tile); `want[i]` is the event capacity item i asks for.  The
+// scratch is the library's own, per device.  Items of a chain whose events
+// do not fit the scratch (a call captured into a CUDA graph before the
+// scratch was large enough) take the direct insert instead.
+int launch_binned_batch(const ItemDesc *items, const uint64_t *want, int n,
+                        const dbg_tuning &tuning, int sm_count, cudaStream_t s, bool fresh);
+
+// Empty the tables of items[0..n) (n <= kBatchItems) with one launch.
+int launch_tables_init(const ItemDesc *items, int n, int sm_count, cudaStream_t s);
+
+// Release the library's own binned scratch on every device (synchronising it).
+int release_batch_scratch();
+
+// Device bytes of the library's own binned scratch on device `dev`.
+uint64_t batch_scratch_bytes(int dev);
 
 // The last binned call's counters (synchronizes the device): out[0] = 1 if
 // the binned kernels did its work, out[1] = events whose probe left their

@@ -94,6 +94,261 @@ __global__ void k_gather(const Slot *t, const I *__restrict__ idx, uint4 *counts
   }
 }
 
+// The prefix sort.  Keys of up to 60 bits are sorted by their top 32 bits
+// only (4 radix passes of 32-bit keys and 32-bit slot indices instead of 8
+// of 64-bit keys: a third less traffic per pass, half the passes).  The
+// gather then writes the keys and counters in that order, and the keys that
+// share a prefix -- reads with an error in a k-mer's last bases give such
+// "siblings" of a genomic k-mer, a few per k-mer at 30x, a hundred in a
+// high-copy repeat -- form runs of the output, each put in key order in
+// place: a thread sorts a short run in registers, a CTA sorts a long one in
+// shared memory.  A run longer than kMaxLongRun (keys crowded into a few
+// prefixes) makes the export fall back to the full-width sort.
+constexpr int kShortRun = 4;      // runs up to this long: one thread, in registers
+constexpr int kWarpRun = 32;      // up to this long: one warp, a register bitonic sort
+constexpr int kMaxLongRun = 2048; // longer runs: the full-width sort instead
+constexpr int kLongBlock = 256;
+
+// K3 for the prefix sort: (top 32 bits of the key, slot index) of every
+// occupied slot, at most `cap` of them; otherwise as k_compact.
+__global__ void __launch_bounds__(kCompactBlock)
+    k_compact_prefix(const Slot *t, uint64_t n_slots, int pshift, uint32_t *prefix, uint32_t *idx,
+                     unsigned long long *count, uint64_t cap) {
+  constexpr int W = kCompactBlock / 32;
+  __shared__ uint32_t s_w[W];
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  constexpr uint64_t kRound = (uint64_t)kCompactBlock * kCompactPer;
+  for (uint64_t base = (uint64_t)blockIdx.x * kRound; base < n_slots;
+       base += (uint64_t)gridDim.x * kRound) {
+    unsigned long long k[kCompactPer];
+    unsigned bal[kCompactPer];
+    uint32_t wcount = 0;
+#pragma unroll
+    for (int r = 0; r < kCompactPer; ++r) {
+      const uint64_t i = base + (uint64_t)r * kCompactBlock + threadIdx.x;
+      k[r] = i < n_slots ? __ldcs(&t[i].key) : kEmpty;
+      bal[r] = __ballot_sync(0xffffffffu, k[r] != kEmpty);
+      wcount += (uint32_t)__popc(bal[r]);
+    }
+    if (lane == 0) s_w[warp] = wcount;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const uint32_t v = s_w[j];
+      before += j < warp ? v : 0u;
+      total += v;
+    }
+    if (threadIdx.x == 0) s_base = total ? atomicAdd(count, (unsigned long long)total) : 0ull;
+    __syncthreads();
+    uint64_t pos = s_base + before;
+#pragma unroll
+    for (int r = 0; r < kCompactPer; ++r) {
+      if (k[r] != kEmpty) {
+        const uint64_t at = pos + (uint64_t)__popc(bal[r] & lt);
+        if (at < cap) {
+          prefix[at] = (uint32_t)(k[r] >> pshift);
+          idx[at] = (uint32_t)(base + (uint64_t)r * kCompactBlock + threadIdx.x);
+        }
+      }
+      pos += (uint64_t)__popc(bal[r]);
+    }
+    __syncthreads();
+  }
+}
+
+// Runs of equal prefixes in the gathered output, each put in key order.  The
+// thread at a run's first position sorts a run of at most kShortRun keys in
+// registers (keys and counter rows together); longer runs are listed, up to
+// kWarpRun long for k_sort_warp_runs, longer for k_sort_long_runs (a full
+// list sets *fallback: the caller then takes the full-width sort).
+__global__ void k_sort_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift,
+                            unsigned long long *mid, unsigned long long *mid_n, uint64_t mid_cap,
+                            unsigned long long *lng, unsigned long long *lng_n, uint64_t lng_cap,
+                            unsigned int *fallback) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // (the loop bound is the block's, so every lane takes part in the ballots)
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const uint64_t i = base + threadIdx.x;
+    uint64_t L = 0;
+    if (i < n) {
+      const uint64_t p = keys[i] >> pshift;
+      if (i == 0 || (keys[i - 1] >> pshift) != p) {  // a run's first position
+        L = 1;
+        while (i + L < n && L <= kWarpRun && (keys[i + L] >> pshift) == p) ++L;
+      }
+    }
+    // longer runs are listed: one atomic per warp and list
+    const bool want_mid = L > kShortRun && L <= kWarpRun, want_lng = L > kWarpRun;
+    const unsigned mm = __ballot_sync(0xffffffffu, want_mid);
+    const unsigned lm = __ballot_sync(0xffffffffu, want_lng);
+    unsigned long long mb = 0, lb = 0;
+    if (lane == 0) {
+      if (mm) mb = atomicAdd(mid_n, (unsigned long long)__popc(mm));
+      if (lm) lb = atomicAdd(lng_n, (unsigned long long)__popc(lm));
+    }
+    mb = __shfl_sync(0xffffffffu, mb, 0);
+    lb = __shfl_sync(0xffffffffu, lb, 0);
+    if (want_mid || want_lng) {
+      const unsigned long long at = want_mid ? mb + __popc(mm & lt) : lb + __popc(lm & lt);
+      if (at < (want_mid ? mid_cap : lng_cap))
+        (want_mid ? mid : lng)[at] = i;
+      else
+        atomicExch(fallback, 1u);
+    }
+    if (L < 2 || L > kShortRun) continue;
+    unsigned long long rk[kShortRun];
+    uint4 rc[kShortRun];
+#pragma unroll
+    for (int a = 0; a < kShortRun; ++a) {
+      rk[a] = a < (int)L ? keys[i + a] : ~0ull;
+      rc[a] = a < (int)L ? counts[i + a] : make_uint4(0u, 0u, 0u, 0u);
+    }
+    // a sorting network over the four places (padding keys of all ones stay last)
+#define DBG_CSWAP(x, y)                        \
+  if (rk[y] < rk[x]) {                         \
+    const unsigned long long tk = rk[x];       \
+    rk[x] = rk[y];                             \
+    rk[y] = tk;                                \
+    const uint4 tc = rc[x];                    \
+    rc[x] = rc[y];                             \
+    rc[y] = tc;                                \
+  }
+    DBG_CSWAP(0, 1) DBG_CSWAP(2, 3) DBG_CSWAP(0, 2) DBG_CSWAP(1, 3) DBG_CSWAP(1, 2)
+#undef DBG_CSWAP
+#pragma unroll
+    for (int a = 0; a < kShortRun; ++a) {
+      if (a < (int)L) {
+        keys[i + a] = rk[a];
+        counts[i + a] = rc[a];
+      }
+    }
+  }
+}
+
+// A warp per listed run of kShortRun + 1 .. kWarpRun keys: lane a holds key
+// a (padding lanes all ones), a bitonic sort over the warp's registers
+// carries each key's lane of origin, and every lane then takes its counter
+// row from that lane.
+__global__ void k_sort_warp_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift,
+                                 const unsigned long long *list, const unsigned long long *list_n) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t runs = *list_n;
+  for (uint64_t r = (((uint64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; r < runs;
+       r += warps) {
+    const uint64_t i = list[r];
+    const uint64_t p = keys[i] >> pshift;
+    const bool in = i + lane < n && (keys[i + lane] >> pshift) == p;
+    const unsigned L = __popc(__ballot_sync(0xffffffffu, in));  // (the run is contiguous from i)
+    unsigned long long k = lane < (int)L ? keys[i + lane] : ~0ull;
+    uint4 row = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < (int)L) row = counts[i + lane];
+    int src = lane;
+    for (int size = 2; size <= 32; size <<= 1) {
+      for (int st = size >> 1; st > 0; st >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, st);
+        const int os = __shfl_xor_sync(0xffffffffu, src, st);
+        const bool lower = (lane & st) == 0;        // this lane keeps the smaller key ...
+        const bool up = (lane & size) == 0;         // ... of an ascending pair
+        const bool take = lower == up ? ok < k : ok > k;
+        if (take) {
+          k = ok;
+          src = os;
+        }
+      }
+    }
+    uint4 mine;
+    mine.x = __shfl_sync(0xffffffffu, row.x, src);
+    mine.y = __shfl_sync(0xffffffffu, row.y, src);
+    mine.z = __shfl_sync(0xffffffffu, row.z, src);
+    mine.w = __shfl_sync(0xffffffffu, row.w, src);
+    if (lane < (int)L) {
+      keys[i + lane] = k;
+      counts[i + lane] = mine;
+    }
+  }
+}
+
+// A CTA per listed run: its keys and positions sorted in shared memory
+// (bitonic, padded to a power of two with keys of all ones), then the keys
+// and counter rows written back in that order.
+__global__ void __launch_bounds__(kLongBlock)
+    k_sort_long_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift,
+                     const unsigned long long *list, const unsigned long long *list_n,
+                     unsigned int *fallback) {
+  __shared__ unsigned long long s_key[kMaxLongRun];
+  __shared__ uint16_t s_pos[kMaxLongRun];
+  __shared__ uint4 s_row[kMaxLongRun];
+  __shared__ uint32_t s_len;
+  const uint64_t runs = *list_n;
+  for (uint64_t r = blockIdx.x; r < runs; r += gridDim.x) {
+    const uint64_t i = list[r];
+    const uint64_t p = keys[i] >> pshift;
+    if (threadIdx.x == 0) {
+      uint64_t L = kWarpRun;  // (longer than that: it was listed)
+      while (i + L < n && L <= kMaxLongRun && (keys[i + L] >> pshift) == p) ++L;
+      s_len = (uint32_t)L;
+      if (L > kMaxLongRun) atomicExch(fallback, 1u);
+    }
+    __syncthreads();
+    const uint32_t L = s_len;
+    if (L > kMaxLongRun) {
+      __syncthreads();
+      continue;
+    }
+    uint32_t P = 1;
+    while (P < L) P <<= 1;
+    for (uint32_t j = threadIdx.x; j < P; j += kLongBlock) {
+      s_key[j] = j < L ? keys[i + j] : ~0ull;
+      s_pos[j] = (uint16_t)j;
+      if (j < L) s_row[j] = counts[i + j];
+    }
+    __syncthreads();
+    for (uint32_t size = 2; size <= P; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t j = threadIdx.x; j < P; j += kLongBlock) {
+          const uint32_t o = j ^ stride;
+          if (o > j) {
+            const bool up = (j & size) == 0;
+            const unsigned long long a = s_key[j], b = s_key[o];
+            if ((a > b) == up) {
+              s_key[j] = b;
+              s_key[o] = a;
+              const uint16_t t = s_pos[j];
+              s_pos[j] = s_pos[o];
+              s_pos[o] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t j = threadIdx.x; j < L; j += kLongBlock) {
+      keys[i + j] = s_key[j];
+      counts[i + j] = s_row[s_pos[j]];
+    }
+    __syncthreads();
+  }
+}
+
+// The sorted graph from the sorted slot indices: each slot read once (one
+// sector), its key and counters written in order.
+__global__ void k_gather_slots(const Slot *t, const uint32_t *__restrict__ idx,
+                               unsigned long long *keys, uint4 *counts, uint64_t n) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint4 *sl = reinterpret_cast<const uint4 *>(t + __ldcs(idx + i));
+    const uint4 a = sl[0], b = sl[1];  // key lo, key hi, cnt0, cnt1 | cnt2, cnt3, pad
+    if (keys) __stcs(keys + i, (unsigned long long)a.x | ((unsigned long long)a.y << 32));
+    if (counts) __stcs(counts + i, make_uint4(a.z, a.w, b.x, b.y));
+  }
+}
+
 struct Guard {
   int prev = -1;
   bool changed = false;
@@ -122,22 +377,41 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// The export of D vertices with slot indices of type I (k <= 32).
+// The sort's temporary bytes for D (key, slot index) pairs of type I.
+template <class I>
+int sort_temp_bytes(uint64_t D, int end_bit, size_t &temp_bytes) {
+  temp_bytes = 0;
+  cub::DoubleBuffer<unsigned long long> dk(nullptr, nullptr);
+  cub::DoubleBuffer<I> dv(nullptr, nullptr);
+  DBG_CK(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, dk, dv, (int64_t)D, 0, end_bit,
+                                         (cudaStream_t)0));
+  return DBG_OK;
+}
+
+// Scratch of an in-place export: [count][sort temp][final indices].
+template <class I>
+int in_place_scratch_bytes(uint64_t D, int end_bit, uint64_t &bytes) {
+  size_t temp = 0;
+  DBG_TRY(sort_temp_bytes<I>(D, end_bit, temp));
+  bytes = 256 + align256(temp) + align256(D * sizeof(I));
+  return DBG_OK;
+}
+
+// The export of D vertices with slot indices of type I (k <= 32).  `caller`
+// (with `caller_bytes`): scratch the caller owns, used instead of the pool
+// (in-place outputs only).
 template <class I>
 int export_pairs(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts_out,
-                 cudaStream_t s) {
+                 cudaStream_t s, void *caller = nullptr, uint64_t caller_bytes = 0) {
   const int end_bit = 2 * (h->k - 1);
   // in place: both outputs on the device, 16-byte aligned (keys_out needs 8,
   // the uint4 rows of counts_out 16), and the index buffers fit beside the
   // second key buffer in counts_out
   const bool in_place = sizeof(I) == 4 && is_device_ptr(keys_out) && is_device_ptr(counts_out) &&
                         ((uintptr_t)keys_out & 15u) == 0 && ((uintptr_t)counts_out & 15u) == 0;
+  if (caller && !in_place) return DBG_ERR_INVALID_ARG;
   size_t temp_bytes = 0;
-  {
-    cub::DoubleBuffer<unsigned long long> dk(nullptr, nullptr);
-    cub::DoubleBuffer<I> dv(nullptr, nullptr);
-    DBG_CK(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, dk, dv, (int64_t)D, 0, end_bit, s));
-  }
+  DBG_TRY(sort_temp_bytes<I>(D, end_bit, temp_bytes));
   const size_t kb = align256(D * sizeof(unsigned long long));
   const size_t ib = align256(D * sizeof(I));
   const size_t cb = align256(D * sizeof(uint4));
@@ -146,7 +420,12 @@ int export_pairs(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts_
   const size_t head = 256 + align256(temp_bytes);
   const size_t total = head + (in_place ? ib : 2 * kb + 2 * ib + cb);
   char *buf = nullptr;
-  DBG_TRY(scratch_alloc(reinterpret_cast<void **>(&buf), total, s));
+  if (caller) {
+    if (caller_bytes < total || ((uintptr_t)caller & 255u)) return DBG_ERR_INVALID_ARG;
+    buf = static_cast<char *>(caller);
+  } else {
+    DBG_TRY(scratch_alloc(reinterpret_cast<void **>(&buf), total, s));
+  }
   unsigned long long *count = reinterpret_cast<unsigned long long *>(buf);
   void *temp = buf + 256;
   I *idx_final = reinterpret_cast<I *>(buf + head);  // (in place only)
@@ -203,11 +482,145 @@ int export_pairs(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts_
       }
     }
   } while (0);
-  cudaError_t e = cudaFreeAsync(buf, s);
+  cudaError_t e = caller ? cudaSuccess : cudaFreeAsync(buf, s);
   if (rc == DBG_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
   e = cudaStreamSynchronize(s);
   if (rc == DBG_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
   return rc;
+}
+
+// The prefix-sort export of D vertices (tables of at most 2^32 slots).
+// Buffers: two (prefix, index) pairs for the sort, the sorted indices, the
+// sort's temporary space, a counter and the long-run flag.  In place (both
+// outputs 16-byte aligned device buffers) the pairs live in keys_out (8
+// bytes a vertex) and counts_out, and the gather writes the outputs
+// directly; otherwise everything is temporary.  Returns DBG_ERR_CAPACITY
+// (not a graph error: the caller falls back to the full-width sort) when a
+// run of equal prefixes is too long.
+int export_prefix(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts_out,
+                  cudaStream_t s, void *caller, uint64_t caller_bytes) {
+  const int bits = 2 * (h->k - 1);
+  const int pshift = bits > 32 ? bits - 32 : 0;
+  const int pbits = bits > 32 ? 32 : bits;
+  const bool in_place = is_device_ptr(keys_out) && is_device_ptr(counts_out) &&
+                        ((uintptr_t)keys_out & 15u) == 0 && ((uintptr_t)counts_out & 15u) == 0;
+  if (caller && !in_place) return DBG_ERR_INVALID_ARG;
+  size_t temp_bytes = 0;
+  {
+    cub::DoubleBuffer<uint32_t> dk(nullptr, nullptr), dv(nullptr, nullptr);
+    DBG_CK(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, dk, dv, (int64_t)D, 0, pbits, s));
+  }
+  const size_t wb = align256(D * sizeof(uint32_t));
+  const uint64_t mid_cap = D / (kShortRun + 1) + 1;  // runs longer than kShortRun, at most
+  const uint64_t list_cap = D / (kWarpRun + 1) + 1;   // runs longer than kWarpRun, at most
+  // scratch: [count, flag, list count][sort temp][sorted indices][long runs],
+  // and without in-place outputs [prefix a][index a][prefix b][index b][keys]
+  // [counters]
+  const size_t head = 256 + align256(temp_bytes);
+  const size_t lb = align256(list_cap * 8) + align256(mid_cap * 8);
+  const size_t total = head + wb + lb +
+                       (in_place ? 0 : 4 * wb + align256(D * 8) + align256(D * sizeof(uint4)));
+  char *buf = nullptr;
+  if (caller) {
+    if (caller_bytes < total || ((uintptr_t)caller & 255u)) return DBG_ERR_INVALID_ARG;
+    buf = static_cast<char *>(caller);
+  } else {
+    DBG_TRY(scratch_alloc(reinterpret_cast<void **>(&buf), total, s));
+  }
+  unsigned long long *count = reinterpret_cast<unsigned long long *>(buf);
+  unsigned int *fallback = reinterpret_cast<unsigned int *>(buf + 8);
+  unsigned long long *list_n = reinterpret_cast<unsigned long long *>(buf + 16);
+  unsigned long long *mid_n = reinterpret_cast<unsigned long long *>(buf + 24);
+  void *temp = buf + 256;
+  uint32_t *idx_final = reinterpret_cast<uint32_t *>(buf + head);
+  unsigned long long *list = reinterpret_cast<unsigned long long *>(buf + head + wb);
+  unsigned long long *mid = list + align256(list_cap * 8) / 8;
+  uint32_t *pa, *ia, *pb, *ib;
+  unsigned long long *keys;
+  uint4 *counts;
+  if (in_place) {
+    char *kb = reinterpret_cast<char *>(keys_out), *cb = reinterpret_cast<char *>(counts_out);
+    pa = reinterpret_cast<uint32_t *>(kb);
+    ia = reinterpret_cast<uint32_t *>(kb + 4 * D);
+    pb = reinterpret_cast<uint32_t *>(cb);
+    ib = reinterpret_cast<uint32_t *>(cb + 4 * D);
+    keys = reinterpret_cast<unsigned long long *>(keys_out);
+    counts = reinterpret_cast<uint4 *>(counts_out);
+  } else {
+    char *p = buf + head + wb + lb;
+    pa = reinterpret_cast<uint32_t *>(p);
+    ia = reinterpret_cast<uint32_t *>(p + wb);
+    pb = reinterpret_cast<uint32_t *>(p + 2 * wb);
+    ib = reinterpret_cast<uint32_t *>(p + 3 * wb);
+    keys = reinterpret_cast<unsigned long long *>(p + 4 * wb);
+    counts = reinterpret_cast<uint4 *>(p + 4 * wb + align256(D * 8));
+  }
+
+  int rc = DBG_OK;
+  unsigned int fallback_host = 0;
+  do {
+    cudaError_t e = cudaMemsetAsync(buf, 0, 32, s);  // count, flag, list counts
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync"); break; }
+    const int sms = std::max(1, h->sm_count);
+    k_compact_prefix<<<sms * 8, kCompactBlock, 0, s>>>(h->table, h->n_slots, pshift, pa, ia, count,
+                                                       D);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { rc = cuda_fail(e, "k_compact_prefix"); break; }
+    cub::DoubleBuffer<uint32_t> dk(pa, pb), dv(ia, ib);
+    e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, dk, dv, (int64_t)D, 0, pbits, s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "DeviceRadixSort::SortPairs"); break; }
+    // the gather overwrites the buffers the sorted indices sit in: move them out
+    e = cudaMemcpyAsync(idx_final, dv.Current(), D * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(indices)"); break; }
+    k_gather_slots<<<sms * 8, 256, 0, s>>>(h->table, idx_final, keys, counts, D);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { rc = cuda_fail(e, "k_gather_slots"); break; }
+    if (pshift > 0) {  // the runs of equal prefixes, in key order
+      k_sort_runs<<<sms * 8, 256, 0, s>>>(keys, counts, D, pshift, mid, mid_n, mid_cap, list,
+                                          list_n, list_cap, fallback);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) { rc = cuda_fail(e, "k_sort_runs"); break; }
+      k_sort_warp_runs<<<sms * 8, 256, 0, s>>>(keys, counts, D, pshift, mid, mid_n);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) { rc = cuda_fail(e, "k_sort_warp_runs"); break; }
+      k_sort_long_runs<<<sms * 4, kLongBlock, 0, s>>>(keys, counts, D, pshift, list, list_n,
+                                                      fallback);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) { rc = cuda_fail(e, "k_sort_long_runs"); break; }
+      e = cudaMemcpyAsync(&fallback_host, fallback, sizeof(fallback_host), cudaMemcpyDeviceToHost,
+                          s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "fall-back flag"); break; }
+      if (fallback_host) { rc = DBG_ERR_CAPACITY; break; }
+    }
+    if (!in_place) {
+      if (keys_out) {
+        e = cudaMemcpyAsync(keys_out, keys, D * sizeof(uint64_t), cudaMemcpyDefault, s);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(keys)"); break; }
+      }
+      if (counts_out) {
+        e = cudaMemcpyAsync(counts_out, counts, D * sizeof(uint4), cudaMemcpyDefault, s);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(counts)"); break; }
+      }
+    }
+  } while (0);
+  cudaError_t e = caller ? cudaSuccess : cudaFreeAsync(buf, s);
+  if (rc == DBG_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
+  e = cudaStreamSynchronize(s);
+  if (rc == DBG_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+  return rc;
+}
+
+// Scratch of an in-place prefix export (see export_prefix).
+int prefix_scratch_bytes(int k, uint64_t D, uint64_t &bytes) {
+  const int bits = 2 * (k - 1);
+  size_t temp = 0;
+  cub::DoubleBuffer<uint32_t> dk(nullptr, nullptr), dv(nullptr, nullptr);
+  DBG_CK(cub::DeviceRadixSort::SortPairs(nullptr, temp, dk, dv, (int64_t)D, 0,
+                                         bits > 32 ? 32 : bits, (cudaStream_t)0));
+  bytes = 256 + align256(temp) + align256(D * sizeof(uint32_t)) +
+          align256((D / (kWarpRun + 1) + 1) * 8) + align256((D / (kShortRun + 1) + 1) * 8);
+  return DBG_OK;
 }
 
 }  // namespace
@@ -228,6 +641,40 @@ extern "C" int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *cou
   if (D > max_n) return DBG_ERR_BUFFER_TOO_SMALL;
   if (D == 0) return DBG_OK;
   if (h->k > 32) return export_sorted_wide(h, D, keys_out, counts_out, s);
-  if (h->n_slots <= 0xFFFFFFFFull) return export_pairs<uint32_t>(h, D, keys_out, counts_out, s);
+  if (h->n_slots <= 0xFFFFFFFFull) {
+    st = export_prefix(h, D, keys_out, counts_out, s, nullptr, 0);
+    if (st != DBG_ERR_CAPACITY) return st;  // (a long run of equal prefixes: full width)
+    return export_pairs<uint32_t>(h, D, keys_out, counts_out, s);
+  }
   return export_pairs<unsigned long long>(h, D, keys_out, counts_out, s);
+}
+
+extern "C" uint64_t dbg_export_scratch_bytes(int k, uint64_t n_vertices, uint64_t n_slots) {
+  using namespace dbg;
+  if (k < 2 || k > 32 || n_slots > 0xFFFFFFFFull) return 0;
+  const uint64_t D = std::max<uint64_t>(n_vertices, 1);
+  uint64_t a = 0, b = 0;  // the prefix sort's, and the full-width fall-back's
+  if (prefix_scratch_bytes(k, D, a) != DBG_OK) return 0;
+  if (in_place_scratch_bytes<uint32_t>(D, 2 * (k - 1), b) != DBG_OK) return 0;
+  return std::max(a, b);
+}
+
+extern "C" int dbg_export_sorted_with(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out,
+                                      uint64_t max_n, uint64_t *n_out, void *scratch,
+                                      uint64_t scratch_bytes, void *stream) {
+  using namespace dbg;
+  if (!h || !n_out || h->k > 32 || h->n_slots > 0xFFFFFFFFull) return DBG_ERR_INVALID_ARG;
+  Guard g(h->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  uint64_t D = 0;
+  int st = dbg_stats(h, &D, nullptr, stream);
+  if (st != DBG_OK) return st;
+  *n_out = D;
+  if (D > max_n) return DBG_ERR_BUFFER_TOO_SMALL;
+  if (D == 0) return DBG_OK;
+  if (!keys_out || !counts_out || !scratch) return DBG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = export_prefix(h, D, keys_out, counts_out, s, scratch, scratch_bytes);
+  if (st != DBG_ERR_CAPACITY) return st;  // (a long run of equal prefixes: full width)
+  return export_pairs<uint32_t>(h, D, keys_out, counts_out, s, scratch, scratch_bytes);
 }

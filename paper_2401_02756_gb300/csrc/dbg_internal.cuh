@@ -63,7 +63,7 @@ struct ItemDesc {
   int k;
   uint64_t tile_begin;       // first global tile index of this item
   int vec_ok;                // packed is 16-byte aligned: vector loads allowed
-  int pad_;
+  int region0;               // binned insert: the item's first region in its chain
   SpillRecord *spill;        // vertices that found no slot go here (null: fail instead)
   uint64_t spill_cap;
   unsigned long long *spill_count;
@@ -181,6 +181,23 @@ __device__ __forceinline__ bool find_or_claim(Slot *table, uint64_t n_slots, uin
 }
 
 
+// Scratch of the binned insert: event buffers and bookkeeping, owned by a
+// handle (its single-read-set inserts) or by the library (batched inserts).
+struct BinScratch {
+  uint64_t *ev = nullptr;               // events, 8 bytes each
+  uint64_t cap = 0;                     // capacity in events
+  uint64_t *ev2 = nullptr;              // tiled apply: events again, grouped by table tile
+  void *aux = nullptr;                  // tiled apply: units, tile buckets, region table
+  uint64_t aux_bytes = 0;
+  unsigned long long *meta = nullptr;   // region counts, ranges, cursors, flag
+  unsigned long long *counters = nullptr;  // the last call's overflow and deferred counts
+                                           // (tiled apply; null otherwise)
+  cudaEvent_t done = nullptr;           // orders the calls that share the scratch
+};
+
+// Release a scratch's buffers (the caller synchronises first).
+void free_bin_scratch(BinScratch &sc);
+
 }  // namespace dbg
 
 // The handle.
@@ -208,16 +225,10 @@ struct dbg_graph {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
-  // binned insert scratch (allocated when a binned insert first needs it)
-  uint64_t *bin_ev = nullptr;               // events, 8 bytes each
-  uint64_t bin_cap = 0;                     // capacity in events
-  uint64_t *bin_ev2 = nullptr;              // tiled apply: events again, grouped by table tile
-  void *bin_aux = nullptr;                  // tiled apply: units, tile buckets, counters
-  unsigned long long *bin_counters = nullptr;  // the last binned call's overflow and deferred
-                                               // counts (tiled apply; null otherwise)
-  uint64_t bin_aux_bytes = 0;
-  unsigned long long *bin_meta = nullptr;   // region counts, ranges, cursors, flag
-  cudaEvent_t bin_done = nullptr;           // orders binned calls that share the scratch
+  // binned insert scratch (allocated when a single-read-set binned insert
+  // first needs it; batched inserts use the library's own)
+  dbg::BinScratch bin;
+  uint64_t bin_want = 0;                    // events asked for by dbg_reserve_events (0: default)
   // optional per-kernel timing of insert calls (dbg_enable_kernel_timing)
   int timer_cap = 0;                        // calls kept
   int timer_calls = 0;                      // calls recorded (may exceed timer_cap)
@@ -244,6 +255,10 @@ int cuda_fail(cudaError_t e, const char *what);
 // Temporary device memory from the library's stream-ordered pool (free it
 // with cudaFreeAsync on a stream).
 int scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+// Give the pools' cached memory back to the device (synchronising each device).
+int release_scratch_pools();
+// Device bytes the pool of device `dev` holds now.
+uint64_t pool_reserved_bytes(int dev);
 int launch_grow(dbg_handle h, uint64_t new_capacity, cudaStream_t s);
 
 // Propagate a non-OK status from a library call.
@@ -265,7 +280,8 @@ ItemDesc make_item(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
 
 // Items passed to one insert launch by value (kernel parameter space), so a
 // launch needs no descriptor upload.  N = 1 for a single read set; batches
-// are cut into launches of at most kBatchItems items.
+// are cut into launches of at most kBatchItems items (ItemPack<128> is 14 KB
+// of the 32 KB parameter space).
 constexpr int kBatchItems = 128;
 template <int N>
 struct ItemPack {

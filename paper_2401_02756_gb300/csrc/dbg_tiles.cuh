@@ -51,6 +51,7 @@ struct VertexCtx {
   SpillRecord *spill;
   uint64_t spill_cap;
   unsigned long long *spill_count;
+  int region0;  // the item's first region (binned insert)
 };
 
 __device__ __forceinline__ uint4 ldg_stream_v4(const uint8_t *p) {
@@ -148,7 +149,8 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
       const uint64_t origin = s_item.origin;
       const VertexCtx ctx{s_item.table,      s_item.n_slots,   s_item.status,
                           s_item.max_probes, s_item.k,         s_item_idx,
-                          s_item.spill,      s_item.spill_cap, s_item.spill_count};
+                          s_item.spill,      s_item.spill_cap, s_item.spill_count,
+                          s_item.region0};
       const int k = ctx.k, m = k - 1;
       const uint64_t nbytes = s_nbytes;
       const int vec_ok = s_item.vec_ok;
@@ -267,7 +269,24 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
                 if (valid) {
                   bool fresh = !have;
                   if (fresh || v >= vr1) {
-                    while (s_vrel[r + 1] <= v) ++r;
+                    if (R > 1 && fresh) {
+                      // a run's first position: R * BLOCK positions (tens of
+                      // reads) past the previous round's, so its read is
+                      // found by binary search -- the last read of the
+                      // sub-tile starting at or before v (measured: scatter
+                      // 16.3 -> 15.3 ms at 100 Mbp against the linear walk)
+                      int lo = r, hi = rb - 1;
+                      while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_vrel[mid] <= v)
+                          lo = mid;
+                        else
+                          hi = mid - 1;
+                      }
+                      r = lo;
+                    } else {  // the next read (or, one position a round, a few reads on)
+                      while (s_vrel[r + 1] <= v) ++r;
+                    }
                     vr1 = s_vrel[r + 1];
                     q = s_prel[r] + (v - s_vrel[r]);
                     qend = s_prel[r + 1];

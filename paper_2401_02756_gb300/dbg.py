@@ -31,8 +31,10 @@ EXPORTED = [
     "dbg_set_spill",
     "dbg_grow",
     "dbg_insert_reads", "dbg_insert_reads_host", "dbg_build_reads", "dbg_build_reads_host",
-    "dbg_insert_batch", "dbg_get_status", "dbg_stats",
-    "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_normalize", "dbg_find_contigs", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
+    "dbg_insert_batch", "dbg_build_batch", "dbg_release_scratch", "dbg_scratch_bytes",
+    "dbg_get_status", "dbg_stats",
+    "dbg_export_sorted", "dbg_export_sorted_noalloc", "dbg_export_scratch_bytes",
+    "dbg_export_sorted_with", "dbg_normalize", "dbg_find_contigs", "dbg_pack_ascii", "dbg_strerror", "dbg_last_cuda_error",
     "dbg_probe_random_sectors", "dbg_probe_window", "dbg_sketch_reads", "dbg_sketch_batch",
     "dbg_sketch_estimate",
     "dbg_mlp_work_floats", "dbg_mlp_features", "dbg_mlp_init", "dbg_mlp_forward",
@@ -57,7 +59,8 @@ class Tuning(ctypes.Structure):
                 ("insert_path", ctypes.c_int), ("apply_unroll", ctypes.c_int),
                 ("apply_chunk", ctypes.c_int), ("apply_ctas", ctypes.c_int),
                 ("apply_counters", ctypes.c_int), ("region_log2", ctypes.c_int),
-                ("apply_group", ctypes.c_int), ("apply_mode", ctypes.c_int)]
+                ("apply_group", ctypes.c_int), ("apply_mode", ctypes.c_int),
+                ("scatter_reads", ctypes.c_int), ("split_threads", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -109,10 +112,15 @@ def load() -> ctypes.CDLL:
         "dbg_build_reads": (I, [P, P, P, U64, P]),
         "dbg_build_reads_host": (I, [P, P, P, U64, P]),
         "dbg_insert_batch": (I, [ctypes.POINTER(BatchItem), I, P]),
+        "dbg_build_batch": (I, [ctypes.POINTER(BatchItem), I, P]),
+        "dbg_release_scratch": (I, []),
+        "dbg_scratch_bytes": (U64, []),
         "dbg_get_status": (I, [P, P]),
         "dbg_stats": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
         "dbg_export_sorted": (I, [P, P, P, U64, ctypes.POINTER(U64), P]),
         "dbg_export_sorted_noalloc": (I, [P, P, P, U64, ctypes.POINTER(U64), P]),
+        "dbg_export_scratch_bytes": (U64, [I, U64, U64]),
+        "dbg_export_sorted_with": (I, [P, P, P, U64, ctypes.POINTER(U64), P, U64, P]),
         "dbg_normalize": (I, [P, ctypes.c_double, P]),
         "dbg_find_contigs": (I, [P, P, U64, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
         "dbg_pack_ascii": (I, [ctypes.c_char_p, U64, P, I, ctypes.POINTER(U64)]),
@@ -247,7 +255,7 @@ class Graph:
 
     TUNING_FIELDS = ("block_threads", "tile_reads", "grid_ctas", "warp_aggregate", "insert_path",
                      "apply_unroll", "apply_chunk", "apply_ctas", "apply_counters", "region_log2",
-                     "apply_group", "apply_mode")
+                     "apply_group", "apply_mode", "scatter_reads", "split_threads")
 
     def set_tuning(self, **fields) -> None:
         """Launch shape and path of the insert; fields (all optional, 0 = automatic):
@@ -255,8 +263,10 @@ class Graph:
         ``insert_path`` (1 direct, 2 binned), ``apply_unroll`` (2/4/8 probe slots per
         thread), ``apply_chunk`` (4/8/16 events per thread per chunk), ``apply_ctas``
         (CTAs per SM), ``apply_counters`` (1..64), ``region_log2`` (16..26),
-        ``apply_group`` (regions per apply launch).  The
-        built graph does not depend on any of these."""
+        ``apply_group`` (regions per apply launch), ``apply_mode`` (1 streaming, 2 tiled),
+        ``scatter_reads`` (the binned scatter's reads per tile, 32..512), ``split_threads``
+        (the split's CTA size, 256/512/1024).  The built graph does not depend on any of
+        these."""
         unknown = set(fields) - set(self.TUNING_FIELDS)
         if unknown:
             raise ValueError(f"unknown tuning fields {sorted(unknown)}")
@@ -412,6 +422,18 @@ class Graph:
                                         ctypes.byref(n), _stream(stream)), "dbg_export_sorted")
         return int(n.value)
 
+    def export_with(self, keys, counts, scratch, stream=None) -> int:
+        """dbg_export_sorted_with: into caller-owned CUDA tensors (keys int64
+        [>= D], counts int32 [>= D, 4], scratch uint8 of at least
+        ``export_scratch_bytes(k, D, n_slots)`` bytes); returns D."""
+        n = ctypes.c_uint64()
+        rows = min(int(keys.shape[0]), int(counts.shape[0]))
+        _check(load().dbg_export_sorted_with(self.handle, keys.data_ptr(), counts.data_ptr(), rows,
+                                             ctypes.byref(n), scratch.data_ptr(),
+                                             int(scratch.numel()), _stream(stream)),
+               "dbg_export_sorted_with")
+        return int(n.value)
+
     def export_device(self, stream=None):
         """Sorted vertices as CUDA tensors (int64 keys [D], or [D, 2] for k > 32;
         int32 counters [D, 4])."""
@@ -430,12 +452,38 @@ class Graph:
         return keys, counts
 
 
-def insert_batch(items, stream=None) -> None:
-    """``items``: list of ``(graph, packed, offsets)`` with device buffers."""
+def _batch_items(items):
     arr = (BatchItem * max(1, len(items)))()
     for i, (g, pk, of) in enumerate(items):
         arr[i] = BatchItem(g.handle, _dptr(pk) or None, _dptr(of) or None, int(of.numel()) - 1)
-    _check(load().dbg_insert_batch(arr, len(items), _stream(stream)), "dbg_insert_batch")
+    return arr
+
+
+def insert_batch(items, stream=None) -> None:
+    """``items``: list of ``(graph, packed, offsets)`` with device buffers."""
+    _check(load().dbg_insert_batch(_batch_items(items), len(items), _stream(stream)),
+           "dbg_insert_batch")
+
+
+def build_batch(items, stream=None) -> None:
+    """dbg_build_batch: every graph emptied, then built from its reads."""
+    _check(load().dbg_build_batch(_batch_items(items), len(items), _stream(stream)),
+           "dbg_build_batch")
+
+
+def export_scratch_bytes(k: int, n_vertices: int, n_slots: int) -> int:
+    """Bytes of caller scratch dbg_export_sorted_with needs."""
+    return int(load().dbg_export_scratch_bytes(int(k), int(n_vertices), int(n_slots)))
+
+
+def scratch_bytes() -> int:
+    """Device bytes the library holds between calls on the current device."""
+    return int(load().dbg_scratch_bytes())
+
+
+def release_scratch() -> None:
+    """Give back the batched inserts' buffers and the export's cached memory."""
+    _check(load().dbg_release_scratch(), "dbg_release_scratch")
 
 
 def probe_random_sectors(buf, n_slots: int, n_ops: int, seed: int, mode: int, stream=None) -> None:

@@ -28,7 +28,11 @@ from . import dbg
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(_HERE, "predictor_weights.npz")
+REPORT = os.path.join(_HERE, "predictor_weights.json")
 REG_STRIDE = dbg.SKETCH_REGISTERS + 1  # registers plus the status word
+# HyperLogLog with 1024 registers has a relative standard error of 1.04 / 32
+# (3.25 %); its margin covers 4.6 of them
+HLL_MARGIN = 1.15
 
 
 @dataclass
@@ -56,6 +60,16 @@ class CapacityPredictor:
             raise ValueError(f"expected {dbg.MLP_PARAMS} parameters")
         self.params = params
         self.margin = 1.0 if margin is None else float(margin)
+        # the distinct-vertex counts the network was trained on: outside them
+        # (a read set far larger than any training sample) the HyperLogLog
+        # estimate sizes the table instead
+        self.trained_range = (0.0, float("inf"))
+        if os.path.exists(REPORT):
+            import json
+            with open(REPORT) as f:
+                dv = json.load(f).get("distinct_vertices", {})
+            if "min" in dv and "max" in dv:
+                self.trained_range = (float(dv["min"]), float(dv["max"]))
         self._work: dict[int, tuple] = {}
 
     def _buffers(self, batch: int):
@@ -95,8 +109,18 @@ class CapacityPredictor:
         regs = dbg.sketch(k, packed, offsets, stream=stream)
         return self.predict_registers(regs, 1, stream=stream)[0]
 
+    def vertices(self, prediction: Prediction) -> float:
+        """The count a table is sized for: the network's prediction times its
+        margin, or -- when the HyperLogLog estimate lies beyond the counts the
+        network was trained on by more than a quarter -- the estimate times
+        HLL_MARGIN."""
+        lo, hi = self.trained_range
+        if prediction.hll > 1.25 * hi or prediction.hll < lo / 1.25:
+            return prediction.hll * HLL_MARGIN
+        return prediction.mlp * self.margin
+
     def capacity(self, prediction: Prediction, headroom: float = 1.5) -> int:
-        """Table slots for a predicted count: margin times headroom times the
-        prediction (the headroom keeps the load factor, and so the probe
-        lengths, where the builder expects them)."""
-        return max(64, int(math.ceil(prediction.mlp * self.margin * headroom)))
+        """Table slots for a predicted count: headroom times ``vertices``
+        (the headroom keeps the load factor, and so the probe lengths, where
+        the builder expects them)."""
+        return max(64, int(math.ceil(self.vertices(prediction) * headroom)))

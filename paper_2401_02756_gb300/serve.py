@@ -17,7 +17,10 @@ Stages of one request, each on its own CUDA stream:
    capacity) is reserved against the budget, laid out in memory taken from
    the PyTorch caching allocator (``dbg_create_on``: no cudaMalloc, no
    device synchronisation), and built with every other ready request in one
-   ``dbg_insert_batch`` call.
+   ``dbg_insert_batch`` call: binned chains that take all of the batch's
+   tables in one launch of each binned kernel, each request's event room
+   (its vertex positions, counted on the host) reserved towards the
+   library's chain buffers.
 3. **export** -- a worker thread checks the status, exports the sorted graph
    into pinned host buffers and hands it to the caller's sink, then
    releases the request's memory.  Tables stay device-resident until then.
@@ -25,12 +28,14 @@ Stages of one request, each on its own CUDA stream:
 Overflow is handled exactly: a table whose status reports that it ran out of
 room is rebuilt at twice the capacity from the request's resident inputs.
 
-Footprint admitted = packed bytes + offsets bytes + registers + table
-bytes, held under ``budget_bytes``; each export adds its device output
-buffers (24 bytes a vertex) and the library's sort scratch (4 bytes a
-vertex) while it runs.  Every device byte the server uses comes from the
-PyTorch allocator except that scratch; a report gives both the accounted
-peak and the allocator's own.
+Footprint admitted = packed bytes + offsets bytes + registers + table bytes
++ the export's device buffers (24 bytes a vertex) and the library's sort
+scratch (4 bytes a vertex) for the vertices the table is sized for, held
+under ``budget_bytes`` together with the buffers the library keeps for the
+binned chains (``dbg_scratch_bytes``; they grow to the largest batch and
+stay): a batch is cut short when the growth it needs does not fit.  Every
+device byte the server uses comes from the PyTorch allocator except the
+library's; a report gives both the accounted peak and the allocator's own.
 """
 
 from __future__ import annotations
@@ -45,7 +50,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import dbg
-from .predictor import REG_STRIDE, CapacityPredictor
+from .predictor import REG_STRIDE, CapacityPredictor, Prediction
 
 
 @dataclass
@@ -111,17 +116,44 @@ def _round(n: int) -> int:
     return (int(n) + 511) // 512 * 512
 
 
+EXPORT_BYTES_PER_VERTEX = 8 + 16 + 4  # device keys and counters, and the sort's index scratch
+EXPORT_BYTES_FIXED = 8 << 20          # the sort's histograms, at most (checked per export)
+
+
+def chain_events(positions: int) -> int:
+    """Events a binned chain reserves for a read set of ``positions`` vertex
+    positions (dbg_reserve_events: the positions plus its bucket margin)."""
+    return positions + positions // 16 + 65536 + 256 * 2048
+
+
+def chain_scratch_bytes(events: int) -> int:
+    """Device bytes of the library's chain buffers for ``events`` events, a
+    little over: the first event buffer (8 bytes each), the second (1.125
+    times as large plus 2^20 events) and about 48 MB of bookkeeping."""
+    return int((8 * events + 8 * (events + events // 8 + (1 << 20)) + (48 << 20)) * 1.03)
+
+
+def table_footprint(capacity: int, expected_vertices: float) -> int:
+    """Device bytes a request's table accounts for from its build to the end
+    of its export: the table, and the export's device buffers for the
+    vertices it is expected to hold."""
+    return (_round(dbg.table_bytes(capacity)) +
+            _round(expected_vertices * EXPORT_BYTES_PER_VERTEX + EXPORT_BYTES_FIXED))
+
+
 class _Job:
     """A request in flight: its device inputs, table and timing."""
 
     __slots__ = ("req", "timing", "packed", "offsets", "regs", "reserved", "table_bytes",
-                 "capacity", "graph", "mem", "ingest_ev")
+                 "export_bytes", "capacity", "graph", "mem", "ingest_ev", "positions")
 
     def __init__(self, req: Request, timing: Timing):
         self.req, self.timing = req, timing
         self.packed = self.offsets = self.regs = self.graph = self.mem = self.ingest_ev = None
-        self.reserved = self.table_bytes = 0
+        self.reserved = self.table_bytes = self.export_bytes = 0
         self.capacity = 0
+        ln = np.diff(req.offsets.astype(np.int64))
+        self.positions = int(np.maximum(ln - req.k + 2, 0).sum())
 
 
 class _Exporter:
@@ -145,9 +177,16 @@ class _Exporter:
             self.rows = rows
         return self.keys, self.counts
 
+    @staticmethod
+    def scratch_need(graph, n: int) -> int:
+        """Device bytes of the export's sort scratch for ``n`` vertices."""
+        return dbg.export_scratch_bytes(graph.k, max(1, n), graph.info()["n_slots"])
+
     def export(self, graph, n: int, s):
         """The sorted graph of ``n`` vertices in pinned host memory: exported
-        into device buffers on ``s``, then copied; views [:n] are returned."""
+        into device buffers on ``s`` (dbg_export_sorted_with: every byte from
+        the PyTorch allocator, none from the library's pool), then copied;
+        views [:n] are returned."""
         import torch
         keys, counts = self.buffers(max(1, n))
         if n == 0:
@@ -155,7 +194,8 @@ class _Exporter:
         with torch.cuda.stream(s):
             kd = torch.empty(n, dtype=torch.int64, device=s.device)
             cd = torch.empty((n, 4), dtype=torch.int32, device=s.device)
-        if graph.export_into(kd, cd, s) != n:
+            scratch = torch.empty(self.scratch_need(graph, n), dtype=torch.uint8, device=s.device)
+        if graph.export_with(kd, cd, scratch, s) != n:
             raise RuntimeError("export: vertex count changed")
         with torch.cuda.stream(s):
             self.keys_t[:n].copy_(kd, non_blocking=True)
@@ -169,9 +209,11 @@ class BuildServer:
 
     def __init__(self, predictor: CapacityPredictor | None = None, budget_bytes: float = 150e9,
                  headroom: float = 1.5, max_batch: int = 128, export_workers: int = 4,
-                 device="cuda"):
+                 device="cuda", tuning: dict | None = None):
         import torch
         self.device = torch.device(device)
+        self.tuning = dict(tuning or {})  # every table's launch shape (autotune.tune_batch)
+        self._lib = 0  # bytes accounted for the library's chain buffers
         self.predictor = predictor or CapacityPredictor(device=device)
         self.budget = int(budget_bytes)
         self.headroom = headroom
@@ -214,39 +256,63 @@ class BuildServer:
                 j.timing.admitted = now
             y = self.predictor.log_vertices(regs, len(jobs), stream=s)
             y_host = torch.empty(len(jobs), dtype=torch.float32, pin_memory=True)
-            st_host = torch.empty(len(jobs), dtype=torch.int32, pin_memory=True)
+            regs_host = torch.empty(regs.shape, dtype=torch.int32, pin_memory=True)
             y_host.copy_(y, non_blocking=True)
-            st_host.copy_(regs[:, -1].contiguous(), non_blocking=True)
+            regs_host.copy_(regs, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
         for j in jobs:
             j.regs = regs
             j.ingest_ev = ev
-        return jobs, (y_host, st_host), ev
+        return jobs, (y_host, regs_host), ev
 
     def _size(self, jobs, out) -> None:
-        y_host, st_host = (t.numpy() for t in out)
+        y_host, regs_host = out[0].numpy(), out[1].numpy()
         for i, j in enumerate(jobs):
-            if int(st_host[i]) != dbg.OK:
-                raise dbg.DbgError(int(st_host[i]), f"sketch of request {j.req.rid}")
-            pred = math.exp(float(y_host[i]))
-            j.capacity = max(64, int(math.ceil(pred * self.predictor.margin * self.headroom)))
+            if int(regs_host[i, -1]) != dbg.OK:
+                raise dbg.DbgError(int(regs_host[i, -1]), f"sketch of request {j.req.rid}")
+            p = Prediction(math.exp(float(y_host[i])),
+                           dbg.sketch_estimate(regs_host[i, :dbg.SKETCH_REGISTERS].view(np.uint32)))
+            j.capacity = self.predictor.capacity(p, self.headroom)
 
-    def _make_table(self, j: _Job, capacity: int, s, force: bool = False) -> bool:
+    def _make_table(self, j: _Job, capacity: int, s, force: bool = False,
+                    lib_extra: int = 0, direct: bool = False) -> bool:
         """Reserve and lay out a table for the job, initialised on stream ``s``;
-        False if it does not fit in the budget (unless ``force``)."""
+        False if it does not fit in the budget (unless ``force``).  The
+        reservation covers the export's buffers too (``table_footprint``),
+        for as many vertices as the table was sized for, and ``lib_extra``
+        bytes of growth of the library's chain buffers."""
         import torch
-        nbytes = _round(dbg.table_bytes(capacity))
-        if not self._reserve(nbytes, force):
+        # (the prediction times its margin: the most vertices it allows for)
+        nbytes = table_footprint(capacity, capacity / self.headroom)
+        if not self._reserve(nbytes + lib_extra, force):
             return False
+        with self._lock:
+            self._lib += lib_extra
         j.reserved += nbytes
         j.table_bytes = nbytes
+        j.export_bytes = nbytes - _round(dbg.table_bytes(capacity))
         with torch.cuda.stream(s):
             j.mem = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         j.graph = dbg.Graph(j.req.k, capacity, memory=j.mem, stream=s)
-        j.graph.set_tuning(insert_path=1)  # the batched direct insert for every request
+        if direct:  # the batch's chain buffers would not fit the budget
+            j.graph.set_tuning(insert_path=1)
+        else:
+            if self.tuning:
+                j.graph.set_tuning(**self.tuning)
+            j.graph.reserve_events(j.positions)  # (its share of the chain buffers: no allocation)
         j.capacity = j.timing.capacity = capacity
         return True
+
+    def _sync_library_bytes(self) -> None:
+        """Account what the library really holds (its buffers grew to a batch's
+        chain: taken even past the budget; the report's peak shows it)."""
+        held = dbg.scratch_bytes()
+        with self._lock:
+            if held > self._lib:
+                self._used += held - self._lib
+                self._lib = held
+                self._peak = max(self._peak, self._used)
 
     def _launch(self, batch: list[_Job]) -> object:
         import torch
@@ -280,6 +346,7 @@ class BuildServer:
             j.reserved -= j.table_bytes
             j.timing.rebuilds += 1
             self._make_table(j, 2 * j.capacity, s, force=True)
+            j.graph.set_tuning(insert_path=1)  # (alone: the direct insert, no chain buffers)
             j.graph.insert(j.packed, j.offsets, stream=s)
         # the sorted export: into device buffers from the allocator (the sort
         # then runs inside them, with 4 bytes a vertex of library scratch),
@@ -287,7 +354,9 @@ class BuildServer:
         # memory.  Only the export workers release memory, so this takes its
         # room even past the budget rather than wait (the peak shows it).
         nv, ne = j.graph.stats(s)
-        xb = _round(nv * (8 + 16 + 4))
+        # (reserved with the table for the expected vertex count; more
+        # vertices than that take the difference, past the budget if need be)
+        xb = max(0, _round(nv * 24 + ex.scratch_need(j.graph, nv)) - j.export_bytes)
         self._reserve(xb, force=True)
         try:
             keys, counts = ex.export(j.graph, nv, s)
@@ -316,6 +385,15 @@ class BuildServer:
         n = len(reqs)
         timings = {r.rid: Timing(r.rid, r.arrival if realtime else 0.0) for r in reqs}
         report = Report()
+        # the library's buffers count against the budget; more of them than
+        # a third of it (left by earlier work in this process) are given back
+        # first (dbg_release_scratch synchronises the device)
+        if dbg.scratch_bytes() > self.budget / 3:
+            dbg.release_scratch()
+            with self._lock:
+                self._used -= self._lib
+                self._lib = 0
+        self._sync_library_bytes()
         with self._lock:
             self._peak = self._used  # the peak of this run only
         torch.cuda.reset_peak_memory_stats(self.device)
@@ -371,18 +449,35 @@ class BuildServer:
                     jobs, out, _ = ingesting.popleft()
                     self._size(jobs, out)
                     sized.extend(jobs)
-                # 3. tables for sized jobs while memory allows, then one batched insert
+                # 3. tables for sized jobs while memory allows (with the growth
+                #    of the library's chain buffers the batch needs), then one
+                #    batched insert
                 batch = []
+                events = 0
+                direct = None  # the batch's first request decides: chains or direct
                 while sized and len(batch) < self.max_batch:
+                    j = sized[0]
                     # with nothing in flight no memory will come back: the
                     # head request then takes its table past the budget
                     force = in_flight == 0 and not batch
-                    if not self._make_table(sized[0], sized[0].capacity, self.s_build, force):
+                    ev = events + chain_events(j.positions)
+                    extra = max(0, chain_scratch_bytes(ev) - self._lib)
+                    if direct is None:
+                        # chain buffers that do not fit now, or would keep more
+                        # than a third of the budget: the direct insert
+                        need = table_footprint(j.capacity, j.capacity / self.headroom)
+                        direct = extra > 0 and (self._used + need + extra > self.budget or
+                                                self._lib + extra > self.budget / 3)
+                    if direct:
+                        extra = 0
+                    if not self._make_table(j, j.capacity, self.s_build, force, extra, direct):
                         break
+                    events = ev
                     batch.append(sized.popleft())
                 if batch:
                     in_flight += len(batch)
                     building.append((batch, self._launch(batch)))
+                    self._sync_library_bytes()
                     report.batches += 1
                     report.batch_sizes.append(len(batch))
                 # 4. builds that completed go to the export workers

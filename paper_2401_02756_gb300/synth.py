@@ -307,6 +307,14 @@ def workload_5mbp(seed: int = 2) -> ReadSet:
     return sample_reads(g, n, 150, 0.01, seed, 31, "5mbp_50x_k31")
 
 
+def workload_2mbp(seed: int = 6) -> ReadSet:
+    """The 100 Mbp workload's reads at a fiftieth of its size, for profiling
+    one kernel at a time: a 2 Mbp uniform genome, 150 bp reads at 30x
+    (400,000 reads), 0.5 % errors, k=31 (a 0.46 GB table at 1.5x)."""
+    g = random_genome(2_000_000, seed)
+    return sample_reads(g, 400_000, 150, 0.005, seed, 31, "2mbp_30x_k31")
+
+
 def workload_100mbp(seed: int = 3) -> ReadSet:
     """100 Mbp genome with 5 % 1-kb repeats (2-50 copies, 0.1 % mutations per
     copy), 150 bp reads at 30x (20,000,000 reads), 0.5 % errors, k=31."""
@@ -358,5 +366,6 @@ WORKLOADS = {
     "fig1": fig1_example,
     "10kb_k21": workload_10kb,
     "5mbp_50x_k31": workload_5mbp,
+    "2mbp_30x_k31": workload_2mbp,
     "100mbp_30x_k31": workload_100mbp,
 }

@@ -38,3 +38,19 @@ def test_default_candidates_cover_both_paths():
     assert {x["insert_path"] for x in c} == {1, 2}
     assert {x.get("apply_mode") for x in c if x["insert_path"] == 2} == {1, 2}
     assert all(x["insert_path"] == 1 for x in autotune.candidates(32, binned=True))
+
+
+def test_tune_batch_picks_a_setting_for_every_graph():
+    sets = [synth.ragged_reads(600 + 300 * i, 220, 21 + 5 * (i % 3), 610 + i) for i in range(5)]
+    graphs = [dbg.Graph(rs.k, capacity_for(rs) + 100_000) for rs in sets]
+    items = [(g, *to_device(rs)) for g, rs in zip(graphs, sets)]
+    settings = autotune.batch_candidates()[:3]
+    best, trials = autotune.tune_batch(items, reps=1, settings=settings)
+    assert best in settings and [t for t, _ in trials] == settings
+    assert all(0 < ms < float("inf") for _, ms in trials)
+    for g, rs in zip(graphs, sets):  # left holding the graphs of the last build
+        assert_same_graph(g.export(), oracle_export(rs))
+    dbg.build_batch(items)
+    for g, rs in zip(graphs, sets):
+        assert_same_graph(g.export(), oracle_export(rs))
+        g.close()

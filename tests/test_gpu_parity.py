@@ -214,3 +214,44 @@ def test_short_and_empty_reads_only():
     rs = synth.from_strings(["ACGTACGTAC"], 10)  # len == k: one edge, two vertices
     got = gpu_export(rs)
     assert got[0].size == 2 and int(got[1].sum()) == 1
+
+
+def test_export_with_caller_scratch():
+    import torch
+    rs = synth.ragged_reads(3000, 250, 31, 4400, lead=2)
+    g = gpu_graph(rs)
+    D, _ = g.stats()
+    keys = torch.empty(D, dtype=torch.int64, device="cuda")
+    counts = torch.empty((D, 4), dtype=torch.int32, device="cuda")
+    xs = dbg.export_scratch_bytes(31, D, g.info()["n_slots"])
+    assert xs >= 4 * D
+    scratch = torch.empty(xs, dtype=torch.uint8, device="cuda")
+    for _ in range(2):  # the scratch holds the first call's contents the second time
+        assert g.export_with(keys, counts, scratch) == D
+        assert_same_graph((keys.cpu().numpy().view(np.uint64), counts.cpu().numpy().view(np.uint32)),
+                          oracle_export(rs))
+    with pytest.raises(dbg.DbgError) as e:  # too small a scratch is refused
+        g.export_with(keys, counts, scratch[:xs // 2])
+    assert e.value.code == dbg.ERR_INVALID_ARG
+    g.close()
+
+
+@pytest.mark.parametrize("n_shared", [20, 200])
+def test_export_keys_sharing_a_prefix(n_shared):
+    # keys of k = 31 are sorted by their top 32 bits (16 bases) first; reads
+    # whose first 16 bases agree give runs of keys with one prefix: 20 of them
+    # are put in order inside the run, 200 (a run over 32) make the export
+    # fall back to the full-width sort -- the same graph either way
+    import torch
+    rng = np.random.default_rng(n_shared)
+    head = "ACGTTGCAAGGCTTAA"
+    reads = [head + "".join(rng.choice(list("ACGT"), size=40)) for _ in range(n_shared)]
+    base = synth.ragged_reads(500, 200, 31, 4500)
+    rs = synth.from_strings(reads + [base.read_ascii(i) for i in range(base.n_reads)], 31)
+    g = gpu_graph(rs)
+    exp = oracle_export(rs)
+    assert_same_graph(g.export(), exp)  # host outputs
+    keys, counts = g.export_device()    # device outputs: the sort runs inside them
+    assert_same_graph((keys.cpu().numpy().view(np.uint64), counts.cpu().numpy().view(np.uint32)),
+                      exp)
+    g.close()

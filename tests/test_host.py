@@ -90,3 +90,21 @@ def test_autotune_candidates():
     assert {c["region_log2"] for c in binned if c["apply_mode"] == 2} == {0, 20, 22}
     # 64-bit events carry keys of at most 60 bits: no binned candidates for k = 32
     assert all(c["insert_path"] == 1 for c in autotune.candidates(32, binned=True))
+
+
+def test_autotune_covers_the_binned_shapes():
+    binned = [c for c in autotune.candidates(31, binned=True) if c.get("apply_mode") == 2]
+    assert {c["scatter_reads"] for c in binned} >= {0, 256, 512}
+    assert {c["split_threads"] for c in binned} >= {0, 1024}
+    batch = autotune.batch_candidates()
+    assert all(c["insert_path"] == 2 and c["apply_mode"] == 2 for c in batch)
+    assert len({tuple(sorted(c.items())) for c in batch}) == len(batch)
+    for c in batch:  # every field is one the C library accepts
+        assert set(c) <= set(bench_tuning_fields())
+        assert c["scatter_reads"] in (0,) or 32 <= c["scatter_reads"] <= 512
+        assert c["split_threads"] in (0, 256, 512, 1024)
+
+
+def bench_tuning_fields():
+    from paper_2401_02756_gb300 import dbg
+    return dbg.Graph.TUNING_FIELDS
