@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="100mbp_30x_k31",
-                    help="100mbp_30x_k31 | 5mbp_50x_k31 | 10kb_k21 | batch256")
+                    help="100mbp_30x_k31 | 5mbp_50x_k31 | 2mbp_30x_k31 | 10kb_k21 | batch256 | "
+                         "serve | sizing64 (--profile-case only)")
     ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serve: device memory budget")
@@ -63,6 +64,8 @@ def parse_args():
     ap.add_argument("--profile-case", action="store_true",
                     help="only build the workload's graph warmup + steps times (a small case "
                          "for ncu) and print a summary line")
+    ap.add_argument("--profile-export", action="store_true",
+                    help="with --profile-case: also export the graph twice into device buffers")
     ap.add_argument("--agg-study", action="store_true",
                     help="time the direct insert with and without warp aggregation and exit")
     ap.add_argument("--probe-sweep", action="store_true",
@@ -559,7 +562,7 @@ def run_ours(args):
             "path_roofline": path_roofline(edges, touches, in_bytes, k1_mean_s, peak, probe,
                                            binned="bin_apply" in kernels),
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
-            "batch256": batch, "serve_poisson200": serve, "serve_100mbp_poisson2": serve_big,
+            "batch256": batch, "serve_poisson200": serve, "serve_100mbp_poisson1": serve_big,
             "gpu_launches": sum(v["launches_per_step"] for v in kernels.values()) * K,
             "kernel_source_digest": kernel_source_digest(),
         }
@@ -909,7 +912,7 @@ def measure_serve(n, rate, budget_gb, steps, seed=31, overload_rate=None):
     }
 
 
-def measure_serve_big(rs, n=6, rate=2.0, budget_gb=150.0, seed=33):
+def measure_serve_big(rs, n=6, rate=1.0, budget_gb=150.0, seed=33):
     """The request loop on requests the size of the 100 Mbp workload (2.4e9
     edges each, all the same reads) arriving at a low Poisson rate: each
     request's table is far beyond what the capacity network was trained on,
@@ -929,11 +932,18 @@ def measure_serve_big(rs, n=6, rate=2.0, budget_gb=150.0, seed=33):
     arrivals = synth.poisson_arrivals(n, rate, seed)
     reqs = [Request(i, rs.k, packed, offsets, float(t), rs.n_edges()) for i, t in enumerate(arrivals)]
     pred = CapacityPredictor()
+    D = workload_distinct(rs.name) or 0
     srv = BuildServer(pred, budget_bytes=budget_gb * 1e9, max_batch=4)
-    srv.run(reqs[:1], realtime=False)  # buffers (library chain, pinned export) grown once
+    srv.reserve_host_rows(int(D * 1.1))  # every worker's pinned output, before the run
+    srv.run(reqs[:1], realtime=False)    # the library's chain buffers grown once
     live = srv.run(reqs, realtime=True).summary()
-    seq = sequential(reqs[:2], pred, realtime=False).summary()
+    from paper_2401_02756_gb300.serve import _Exporter
+    ex = _Exporter(torch.device("cuda"))
+    ex.buffers(int(D * 1.1))
+    sequential(reqs[:1], pred, realtime=False, exporter=ex)  # its own buffers grown once
+    seq = sequential(reqs[:2], pred, realtime=False, exporter=ex).summary()
     return {"config": {"workload": f"serve_100mbp_poisson{rate:g}", "requests": n,
+                       "warm": "pinned outputs and the library's buffers sized before the run",
                        "edges_per_request": rs.n_edges(), "arrival_rate_per_s": rate,
                        "budget_gb": budget_gb,
                        "sizing": "HyperLogLog (beyond the network's training range)",
@@ -971,6 +981,10 @@ def run_profile_case(args):
     _build.build()
     dbg.load()
     torch.cuda.set_device(0)
+    if args.workload == "batch256":
+        return run_profile_batch(args)
+    if args.workload == "sizing64":
+        return run_profile_sizing(args)
     rs = synth.WORKLOADS[args.workload]()
     packed = torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda()
     offsets = torch.from_numpy(rs.offsets.view(np.int64).copy()).cuda()
@@ -991,11 +1005,79 @@ def run_profile_case(args):
     nv, ne = g.stats()
     if g.status() != dbg.OK or nv != D or ne != rs.n_edges():
         raise RuntimeError("profile case: wrong graph")
+    if args.profile_export:
+        keys = torch.empty(nv, dtype=torch.int64, device="cuda")
+        counts = torch.empty((nv, 4), dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            if g.export_into(keys, counts) != nv:
+                raise RuntimeError("profile case: export size")
+        del keys, counts
     print(json.dumps({"workload": args.workload, "tuning": tuning or "default", "builds":
                       args.warmup + args.steps, "vertices": nv, "edges": ne, "touches": touches,
                       "table_slots": g.info()["n_slots"], "binned": g.binned_counters()}),
           flush=True)
     g.close()
+
+
+def run_profile_batch(args):
+    """The batched workload's sizing (sketches, one network forward) and its
+    batched build (dbg_build_batch), warmup + steps times, with the
+    benchmark's chain shape (2^19-slot regions); one summary line."""
+    import torch
+
+    from paper_2401_02756_gb300 import dbg
+    from paper_2401_02756_gb300.predictor import REG_STRIDE, CapacityPredictor
+    samples = gen_batch_samples(256, 4)
+    dev = [(torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda(),
+            torch.from_numpy(rs.offsets.view(np.int64).copy()).cuda()) for rs in samples]
+    pred = CapacityPredictor()
+    regs = torch.zeros(len(samples), REG_STRIDE, dtype=torch.int32, device="cuda")
+    sk = [(rs.k, pk, of, regs[i]) for i, (rs, (pk, of)) in enumerate(zip(samples, dev))]
+    dbg.sketch_batch(sk)
+    graphs = [dbg.Graph(rs.k, pred.capacity(p))
+              for rs, p in zip(samples, pred.predict_registers(regs, len(samples)))]
+    for rs, g in zip(samples, graphs):
+        g.reserve_events(int(np.maximum(rs.lengths() - rs.k + 2, 0).sum()))
+        g.set_tuning(insert_path=2, apply_mode=2, region_log2=19)
+    items = [(g, pk, of) for g, (pk, of) in zip(graphs, dev)]
+    for _ in range(args.warmup + args.steps):
+        dbg.sketch_batch(sk)
+        pred.log_vertices(regs, len(samples))
+        dbg.build_batch(items)
+    torch.cuda.synchronize()
+    if any(g.status() != dbg.OK for g in graphs):
+        raise RuntimeError("profile case: a batched build failed")
+    print(json.dumps({"workload": "batch256", "builds": args.warmup + args.steps,
+                      "graphs": len(graphs), "vertices": sum(g.stats()[0] for g in graphs)}),
+          flush=True)
+    for g in graphs:
+        g.close()
+
+
+def run_profile_sizing(args, n_samples=64):
+    """The batched workload's sizing alone on its first 64 samples (about
+    1.1e9 vertex positions, 0.3 GB of packed bases: larger than L2, small on
+    the device): dbg_sketch_batch and one network forward, warmup + steps
+    times; one summary line."""
+    import torch
+
+    from paper_2401_02756_gb300 import dbg
+    from paper_2401_02756_gb300.predictor import REG_STRIDE, CapacityPredictor
+    samples = gen_batch_samples(n_samples, 4)
+    dev = [(torch.from_numpy(np.concatenate([rs.packed, np.zeros(16, np.uint8)])).cuda(),
+            torch.from_numpy(rs.offsets.view(np.int64).copy()).cuda()) for rs in samples]
+    pred = CapacityPredictor()
+    regs = torch.zeros(len(samples), REG_STRIDE, dtype=torch.int32, device="cuda")
+    sk = [(rs.k, pk, of, regs[i]) for i, (rs, (pk, of)) in enumerate(zip(samples, dev))]
+    for _ in range(args.warmup + args.steps):
+        dbg.sketch_batch(sk)
+        pred.log_vertices(regs, len(samples))
+    preds = pred.predict_registers(regs, len(samples))
+    print(json.dumps({"workload": "sizing64", "sizings": args.warmup + args.steps,
+                      "samples": len(samples),
+                      "positions": int(sum(np.maximum(rs.lengths() - rs.k + 2, 0).sum()
+                                           for rs in samples)),
+                      "predicted_vertices": float(sum(p.mlp for p in preds))}), flush=True)
 
 
 def microsatellite_reads(n_per_period=20000, read_len=150, seed=5):

@@ -69,7 +69,8 @@ typedef struct dbg_tuning {
   int block_threads;  /* threads per CTA, a multiple of 32 in [64, 1024] (default 256) */
   int tile_reads;     /* reads staged per tile, in [1, block_threads] (default block_threads) */
   int grid_ctas;      /* CTAs in the persistent grid (default: SMs x resident CTAs per SM) */
-  int warp_aggregate; /* 1: merge equal keys of a warp with __match_any_sync; 0: off; -1: default */
+  int warp_aggregate; /* direct insert: 1 merges a warp's equal keys with __match_any_sync,
+                         0 does not, -1: default (1) */
   int insert_path;    /* 0: automatic; 1: direct; 2: binned (k <= 31; see dbg_insert_reads) */
   int apply_unroll;   /* binned apply: probe slots per thread, 2, 4 or 8 (0: default 4) */
   int apply_chunk;    /* binned apply: events per thread per work chunk, 4, 8 or 16 (0: 8) */

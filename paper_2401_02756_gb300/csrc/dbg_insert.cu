@@ -13,9 +13,10 @@
 // for a key can count at once: no allocate/retry/free loop (Alg. 3's
 // do-while) is needed, and the result is independent of thread order.
 //
-// Optional warp aggregation (__match_any_sync): lanes of a warp holding the
-// same key probe once (the lowest lane), and lanes adding to the same
-// (slot, label) counter issue one atomicAdd of the group size.
+// Warp aggregation (__match_any_sync; on unless the tuning turns it off):
+// lanes of a warp holding the same key probe once (the lowest lane), and
+// lanes adding to the same (slot, label) counter issue one atomicAdd of the
+// group size.
 //
 // Probing is bounded by max_probes; a vertex that finds neither its key nor
 // an empty slot sets the sticky DBG_ERR_CAPACITY and the CTA stops, and later
@@ -134,7 +135,10 @@ dbg_tuning resolve_tuning(const dbg_tuning &t) {
   dbg_tuning r = t;
   if (r.block_threads <= 0) r.block_threads = 256;
   if (r.tile_reads <= 0 || r.tile_reads > r.block_threads) r.tile_reads = r.block_threads;
-  if (r.warp_aggregate < 0) r.warp_aggregate = 0;
+  // warp aggregation on by default: it costs nothing where a warp's keys
+  // differ (100 Mbp direct insert: 155.9 ms either way) and merges repeats
+  // (microsatellite reads: 0.85 -> 0.18 ms)
+  if (r.warp_aggregate < 0) r.warp_aggregate = 1;
   if (r.apply_unroll <= 0) r.apply_unroll = 4;
   if (r.apply_chunk <= 0) r.apply_chunk = 8;
   if (r.apply_counters <= 0) r.apply_counters = 16;

@@ -226,6 +226,13 @@ class BuildServer:
         self._used = 0
         self._peak = 0
 
+    def reserve_host_rows(self, rows: int) -> None:
+        """Size every export worker's pinned output buffers for graphs of
+        ``rows`` vertices now (pinning host memory takes time: better before
+        requests arrive than on their path)."""
+        for ex in self._exporters:
+            ex.buffers(rows)
+
     # -- memory accounting ------------------------------------------------------
     def _reserve(self, n: int, force: bool = False) -> bool:
         with self._lock:
@@ -519,16 +526,17 @@ class BuildServer:
 
 
 def sequential(requests: list[Request], predictor: CapacityPredictor, sink=None,
-               realtime: bool = True, headroom: float = 1.5) -> Report:
+               realtime: bool = True, headroom: float = 1.5, exporter=None) -> Report:
     """The same requests served one at a time with plain calls: for each, in
     arrival order, copy its reads to the device, sketch and size it, create a
     table, insert, export (into the same kind of reused pinned buffer as the
-    server's), destroy (first come, first served)."""
+    server's; ``exporter`` keeps it across calls), destroy (first come, first
+    served)."""
     import torch
     reqs = sorted(requests, key=lambda r: r.arrival)
     report = Report()
     s = torch.cuda.current_stream()
-    ex = _Exporter(torch.device("cuda"))
+    ex = exporter or _Exporter(torch.device("cuda"))
     t0 = time.perf_counter()
     for r in reqs:
         if realtime:

@@ -63,6 +63,7 @@ def test_stats_match_oracle():
     dict(block_threads=128), dict(block_threads=512), dict(tile_reads=1), dict(tile_reads=7),
     dict(tile_reads=100, block_threads=128), dict(grid_ctas=1), dict(grid_ctas=3),
     dict(warp_aggregate=1), dict(warp_aggregate=1, block_threads=512, tile_reads=33),
+    dict(warp_aggregate=0), dict(warp_aggregate=0, block_threads=128, tile_reads=50),
 ])
 def test_launch_shape_independence(tuning):
     rs = synth.ragged_reads(1500, 220, 31, 77, lead=3)
