@@ -21,6 +21,7 @@ namespace {
 
 constexpr unsigned long long kSketchSalt = 0x9E3779B97F4A7C15ull;
 constexpr int kSketchRegs = DBG_SKETCH_REGISTERS;
+constexpr int kSketchRun = 16;  // positions of one read per thread and round (no visitor state)
 
 __device__ __forceinline__ void sketch_hash(uint64_t key, uint32_t &idx, uint32_t &rho) {
   const uint64_t h = fmix64(key ^ kSketchSalt);
@@ -54,7 +55,8 @@ __global__ void __launch_bounds__(BLOCK)
   for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK) s_reg[j] = 0u;
   __syncthreads();
   SketchVisitor vis{s_reg};
-  for_each_vertex<BLOCK, 1, 8>(pk, tile_reads, smem, vis, blockIdx.x, pk.total_tiles, gridDim.x);
+  for_each_vertex<BLOCK, 1, kSketchRun>(pk, tile_reads, smem, vis, blockIdx.x, pk.total_tiles,
+                                        gridDim.x);
   __syncthreads();
   for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK)
     if (s_reg[j]) atomicMax(&regs[j], s_reg[j]);
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(BLOCK)
     const int it = find_item(pk, t);
     const uint64_t end = it + 1 < pk.n_items ? pk.d[it + 1].tile_begin : pk.total_tiles;
     const uint64_t tb = min(t1, end);
-    for_each_vertex<BLOCK, kBatchItems, 8>(pk, tile_reads, smem, vis, t, tb, 1);
+    for_each_vertex<BLOCK, kBatchItems, kSketchRun>(pk, tile_reads, smem, vis, t, tb, 1);
     __syncthreads();
     uint32_t *g = reinterpret_cast<uint32_t *>(pk.d[it].table);
     for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK)

@@ -10,20 +10,26 @@
 //      coalesced 16-byte loads (a tile wider than the window is cut into
 //      sub-tiles; a single read wider than the window reads its bases from
 //      global memory);
-//   3. maps each thread to a run of R consecutive vertex positions of the
-//      flattened (sub-)tile (inside a window with 32-bit indices relative to
-//      the sub-tile and the window); the first key of a run (or of a read inside it)
+//   3. maps each thread to a run of up to R consecutive vertex positions of
+//      one read (R >= 4: every read is cut into ceil(positions / R) runs, so
+//      a run never crosses a read boundary; inside a window with 32-bit
+//      indices relative to the sub-tile and the window).  A run's first key
 //      is extracted -- the k-1 bases, first base most significant -- from two
-//      64-bit window words with a funnel shift and a 2-bit-group reversal,
-//      and the next ones roll: key' = ((key << 2) | label) & mask, where the
-//      label s_{k-1} of one position is the last base of the next key;
+//      64-bit window words with a funnel shift and a 2-bit-group reversal;
+//      the run's R labels (the label s_{k-1} of a position is the base after
+//      its key, the last base of the next key) come from one more funnel
+//      shift, and the next keys roll: key' = ((key << 2) | label) & mask.
+//      (R < 4, the direct insert: a thread's R positions are consecutive
+//      positions of the flattened sub-tile and may cross reads.)
 //   4. calls vis.vertex(...) for every position, in block-uniform rounds of
-//      BLOCK * R positions, and vis.round_end() after every round.
+//      BLOCK runs, and vis.round_end() after every round.
 // A visitor whose rounds contain __syncthreads sets kUniformRounds; the
 // insert visitor instead may stop a thread early (vis.stop()).  The CTA walks
 // tiles t_first, t_first + t_stride, ... below t_end; every thread of the CTA
 // must call for_each_vertex with the same arguments.
 #pragma once
+
+#include <type_traits>
 
 #include "dbg_internal.cuh"
 
@@ -34,10 +40,11 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Dynamic shared memory the tile machinery uses (the visitor's own region
 // follows it, 16-byte aligned): the window, the reads' offsets and vertex
-// prefix (64-bit), and both again relative to the window (32-bit).
+// prefix (64-bit), both again relative to the window (32-bit), and the
+// reads' run prefix for the tile and relative to the sub-tile (32-bit).
 __host__ __device__ constexpr size_t tile_smem_bytes(int tile_reads) {
   return (size_t)(kWinWords + 2) * 8 + (size_t)(tile_reads + 1) * 16 +
-         (((size_t)(tile_reads + 1) * 8 + 15) & ~(size_t)15);
+         2 * (((size_t)(tile_reads + 1) * 8 + 15) & ~(size_t)15);
 }
 
 // What a visitor learns about the item a vertex belongs to.
@@ -117,12 +124,21 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
   // read starts relative to the window's first base (tile_reads + 1 each)
   uint32_t *s_vrel = reinterpret_cast<uint32_t *>(s_vpre + tile_reads + 1);
   uint32_t *s_prel = s_vrel + tile_reads + 1;
+  // runs (R >= 4): first run of every read, for the tile and for the sub-tile
+  // (modulo 2^32: only differences inside a window-sized sub-tile are used)
+  uint32_t *s_upre = reinterpret_cast<uint32_t *>(
+      reinterpret_cast<unsigned char *>(s_vrel) + (((size_t)(tile_reads + 1) * 8 + 15) & ~(size_t)15));
+  uint32_t *s_urel = s_upre + tile_reads + 1;
+  constexpr bool kAligned = R >= 4;
+  static_assert(!kAligned || ((R & (R - 1)) == 0 && R <= 32), "aligned runs: R a power of two <= 32");
+  using LabelWord = typename std::conditional<(R <= 16), uint32_t, uint64_t>::type;
 
   __shared__ ItemDesc s_item;
   __shared__ int s_item_idx;
   __shared__ uint32_t s_stop;
   __shared__ uint64_t s_nbytes;
   __shared__ uint64_t s_warp[BLOCK / 32];
+  __shared__ uint32_t s_warpu[BLOCK / 32];
   __shared__ int s_rb, s_global;
   __shared__ uint64_t s_wb0;
 
@@ -173,27 +189,50 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
       }
       bad = __syncthreads_or(bad);
       if (!bad) {
+        // runs of the read (R >= 4), modulo 2^32
+        const uint32_t nu = kAligned ? (uint32_t)((nv + (uint64_t)(R - 1)) / (uint64_t)R) : 0u;
         uint64_t incl = nv;
+        uint32_t inclu = nu;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
           const uint64_t o = __shfl_up_sync(kFull, incl, d);
           if (lane >= d) incl += o;
+          if (kAligned) {
+            const uint32_t ou = __shfl_up_sync(kFull, inclu, d);
+            if (lane >= d) inclu += ou;
+          }
         }
-        if (lane == 31) s_warp[warp] = incl;
+        if (lane == 31) {
+          s_warp[warp] = incl;
+          if (kAligned) s_warpu[warp] = inclu;
+        }
         __syncthreads();
         if (warp == 0) {
           uint64_t w = lane < BLOCK / 32 ? s_warp[lane] : 0;
+          uint32_t wu = kAligned && lane < BLOCK / 32 ? s_warpu[lane] : 0u;
 #pragma unroll
           for (int d = 1; d < 32; d <<= 1) {
             const uint64_t o = __shfl_up_sync(kFull, w, d);
             if (lane >= d) w += o;
+            if (kAligned) {
+              const uint32_t ou = __shfl_up_sync(kFull, wu, d);
+              if (lane >= d) wu += ou;
+            }
           }
-          if (lane < BLOCK / 32) s_warp[lane] = w;  // inclusive over warps
+          if (lane < BLOCK / 32) {
+            s_warp[lane] = w;  // inclusive over warps
+            if (kAligned) s_warpu[lane] = wu;
+          }
         }
         __syncthreads();
         const uint64_t excl = incl - nv + (warp > 0 ? s_warp[warp - 1] : 0);
         if (tid < nr) s_vpre[tid] = excl;
         if (tid == nr - 1) s_vpre[nr] = excl + nv;
+        if (kAligned) {
+          const uint32_t exclu = inclu - nu + (warp > 0 ? s_warpu[warp - 1] : 0u);
+          if (tid < nr) s_upre[tid] = exclu;
+          if (tid == nr - 1) s_upre[nr] = exclu + nu;
+        }
         __syncthreads();
 
         // 2-4. sub-tiles whose bases fit the window
@@ -245,12 +284,56 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
             for (int i = ra + tid; i <= rb; i += BLOCK) {
               s_vrel[i] = (uint32_t)(s_vpre[i] - s_vpre[ra]);
               s_prel[i] = (uint32_t)(s_off[i] - origin - (wb0 << 2));
+              if (kAligned) s_urel[i] = s_upre[i] - s_upre[ra];
             }
             __syncthreads();
           }
           const uint64_t v_lo = s_vpre[ra], v_hi = s_vpre[rb];
           const uint64_t mask = (1ull << (2 * m)) - 1ull;
           int r = ra;
+          if (kAligned && !gmode) {
+            // runs of up to R positions of one read: run u of the sub-tile
+            // belongs to the last read whose first run is at or before u
+            const uint32_t n_runs = s_urel[rb];
+            for (uint32_t ub = 0; ub < n_runs; ub += (uint32_t)BLOCK) {
+              if (!Visitor::kUniformRounds && vis.stop(lane)) break;
+              const uint32_t u = ub + (uint32_t)tid;
+              uint64_t key = kEmpty;
+              LabelWord labels = 0;
+              uint32_t cnt = 0, cnt_edge = 0;
+              if (u < n_runs) {
+                int lo = ra, hi = rb - 1;
+                while (lo < hi) {
+                  const int mid = (lo + hi + 1) >> 1;
+                  if (s_urel[mid] <= u)
+                    lo = mid;
+                  else
+                    hi = mid - 1;
+                }
+                const uint32_t j0 = (u - s_urel[lo]) * (uint32_t)R;  // first position in the read
+                const uint32_t nvr = s_vrel[lo + 1] - s_vrel[lo];     // > j0
+                cnt = min((uint32_t)R, nvr - j0);
+                cnt_edge = min((uint32_t)R, nvr - 1u - j0);  // the read's last vertex has no edge
+                const uint32_t q = s_prel[lo] + j0;
+                key = key_from_words(s_win[q >> 5], s_win[(q >> 5) + 1], (q & 31) * 2, m);
+                const uint32_t qe = q + (uint32_t)m;  // base of the first label
+                const uint32_t sh = (qe & 31) * 2;
+                const uint64_t w0 = s_win[qe >> 5], w1 = s_win[(qe >> 5) + 1];
+                labels = (LabelWord)(sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0);
+              }
+#pragma unroll
+              for (int sub = 0; sub < R; ++sub) {
+                const uint32_t label = (uint32_t)(labels >> (2 * sub)) & 3u;
+                vis.vertex((uint32_t)sub < cnt, key, (uint32_t)sub < cnt_edge, label, lane, sub,
+                           ctx);
+                key = ((key << 2) | label) & mask;
+              }
+              if (Visitor::kUniformRounds) vis.round_end();
+            }
+            __syncthreads();
+            ra = rb;
+            continue;
+          }
           if (!gmode) {
             // v: vertex index relative to v_lo; q: base position relative to
             // the window; the read holding v spans vertices [., vr1) and
@@ -269,24 +352,7 @@ __device__ __forceinline__ void for_each_vertex(const ItemPack<N> &pk, int tile_
                 if (valid) {
                   bool fresh = !have;
                   if (fresh || v >= vr1) {
-                    if (R > 1 && fresh) {
-                      // a run's first position: R * BLOCK positions (tens of
-                      // reads) past the previous round's, so its read is
-                      // found by binary search -- the last read of the
-                      // sub-tile starting at or before v (measured: scatter
-                      // 16.3 -> 15.3 ms at 100 Mbp against the linear walk)
-                      int lo = r, hi = rb - 1;
-                      while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_vrel[mid] <= v)
-                          lo = mid;
-                        else
-                          hi = mid - 1;
-                      }
-                      r = lo;
-                    } else {  // the next read (or, one position a round, a few reads on)
-                      while (s_vrel[r + 1] <= v) ++r;
-                    }
+                    while (s_vrel[r + 1] <= v) ++r;  // the next read (or a few reads on)
                     vr1 = s_vrel[r + 1];
                     q = s_prel[r] + (v - s_vrel[r]);
                     qend = s_prel[r + 1];
