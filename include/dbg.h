@@ -330,22 +330,28 @@ int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *strea
  * low word) and counts_out[4*i .. 4*i+3] (labels A, C, G, T).
  * Output pointers may be host or device memory (copied with
  * cudaMemcpyDefault); either may be NULL to skip it.  Waits for `stream`.
- * *n_out receives the number of vertices D.  If D > max_n nothing is
- * written and DBG_ERR_BUFFER_TOO_SMALL is returned (a call with max_n = 0
- * is therefore a size query).  Temporary device memory comes from a
- * stream-ordered pool the library keeps per device (up to 4 GiB of it stays
- * cached between calls) and is released to it before return: 4 bytes per
- * vertex when both outputs are 16-byte aligned device buffers and k <= 32
- * (the sort then runs inside keys_out and counts_out), otherwise about 40
- * bytes per vertex (80 for k > 32).  Errors: INVALID_ARG, OOM, CUDA,
- * BUFFER_TOO_SMALL, and the sticky status (nothing exported when it is set). */
+ * *n_out receives the number of vertices D.  If D > max_n,
+ * DBG_ERR_BUFFER_TOO_SMALL is returned and nothing is exported (a call with
+ * max_n = 0 is therefore a size query); host outputs are then untouched, but
+ * in-place device outputs (below) may have served as scratch.  Temporary
+ * device memory comes from a stream-ordered pool the library keeps per
+ * device (up to 4 GiB of it stays cached between calls) and is released to
+ * it before return: about 6 bytes per vertex (the sorted slot indices and the
+ * lists of runs of keys that share their first 16 bases) when both outputs
+ * are 16-byte aligned device buffers and k <= 32 -- the sort then runs
+ * inside keys_out and counts_out, whose max_n rows it uses, and the
+ * compaction that fills them counts the vertices, so no separate counting
+ * pass over the table is made -- otherwise about 40 bytes per vertex (80 for
+ * k > 32).  Errors: INVALID_ARG, OOM, CUDA, BUFFER_TOO_SMALL, and the sticky
+ * status (nothing exported when it is set). */
 int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out, uint64_t max_n,
                       uint64_t *n_out, void *stream);
 
 /* Device bytes of scratch dbg_export_sorted_with needs for a graph of
  * n_vertices vertices (k <= 32, a table of at most 2^32 slots): the sort's
- * histograms and one slot index per vertex.  0 for arguments it does not
- * take.  Needs a device (the sort sizes its work for it). */
+ * histograms, one slot index per vertex and the lists of runs of keys that
+ * share a prefix.  0 for arguments it does not take.  Needs a device (the
+ * sort sizes its work for it). */
 uint64_t dbg_export_scratch_bytes(int k, uint64_t n_vertices, uint64_t n_slots);
 
 /* dbg_export_sorted with every byte of device memory from the caller: for a
@@ -356,9 +362,11 @@ uint64_t dbg_export_scratch_bytes(int k, uint64_t n_vertices, uint64_t n_slots);
  * `scratch` is a 256-byte aligned device buffer of at least
  * dbg_export_scratch_bytes(k, n, n_slots) bytes, all owned by the caller.
  * k <= 32 and a table of at most 2^32 slots.  Same result and ordering as
- * dbg_export_sorted; waits for `stream`.  Errors: INVALID_ARG (including too
- * small or misaligned scratch and host outputs), CUDA, BUFFER_TOO_SMALL (a
- * size query with max_n = 0), and the sticky status. */
+ * dbg_export_sorted (the vertices are counted by the compaction into the
+ * outputs); waits for `stream`.  Errors: INVALID_ARG (including too small or
+ * misaligned scratch and host outputs), CUDA, BUFFER_TOO_SMALL (a size query
+ * with max_n = 0), and the sticky status.  After an error the outputs'
+ * contents are unspecified. */
 int dbg_export_sorted_with(dbg_handle h, uint64_t *keys_out, uint32_t *counts_out,
                            uint64_t max_n, uint64_t *n_out, void *scratch,
                            uint64_t scratch_bytes, void *stream);

@@ -159,56 +159,116 @@ __global__ void __launch_bounds__(kCompactBlock)
   }
 }
 
-// Runs of equal prefixes in the gathered output, each put in key order.  The
-// thread at a run's first position sorts a run of at most kShortRun keys in
-// registers (keys and counter rows together); longer runs are listed, up to
-// kWarpRun long for k_sort_warp_runs, longer for k_sort_long_runs (a full
-// list sets *fallback: the caller then takes the full-width sort).
-__global__ void k_sort_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift,
-                            unsigned long long *mid, unsigned long long *mid_n, uint64_t mid_cap,
-                            unsigned long long *lng, unsigned long long *lng_n, uint64_t lng_cap,
-                            unsigned int *fallback) {
+// The run pass works on contiguous chunks: kRunCtas CTAs at most, each
+// owning the runs that start in its chunk of `chunk` positions (a multiple of
+// kRunBlock).  Runs too long for a thread go to the CTA's own segments of
+// two lists, counted in shared memory -- no global atomics: the first
+// version appended to one list counter per warp and took 7.3 ms at 100 Mbp,
+// serialised on that counter.
+constexpr int kRunBlock = 256;
+constexpr int kRunCtas = 1216;  // 8 CTAs of 256 threads on each of 152 SMs
+
+struct RunLists {
+  uint64_t chunk;    // positions per CTA
+  int ctas;          // CTAs of the run pass
+  uint64_t mid_cap;  // list entries per CTA: runs of kShortRun + 1 .. kWarpRun keys
+  uint64_t lng_cap;  // runs of more than kWarpRun keys
+  uint64_t bytes() const { return (uint64_t)ctas * (mid_cap + lng_cap) * 8; }
+};
+
+RunLists run_lists(uint64_t D) {
+  RunLists r;
+  const uint64_t per = (D + kRunCtas - 1) / kRunCtas;
+  r.chunk = std::max<uint64_t>(kRunBlock, (per + kRunBlock - 1) / kRunBlock * kRunBlock);
+  r.ctas = (int)std::max<uint64_t>(1, (D + r.chunk - 1) / r.chunk);
+  r.mid_cap = r.chunk / (kShortRun + 1) + 1;  // runs that start in a chunk, at most
+  r.lng_cap = r.chunk / (kWarpRun + 1) + 1;
+  return r;
+}
+
+// Runs of equal prefixes in the gathered output, each put in key order.  A
+// warp finds the run starts among its 32 positions by comparing each prefix
+// with its neighbour's, and a run's length from the next start in the warp
+// (only the warp's last run reads on past it).  The thread at a run's first
+// position sorts a run of at most kShortRun keys in registers (keys and
+// counter rows together; a run already in order is left as it is); longer
+// runs are listed: up to kWarpRun long for k_sort_warp_runs, longer for
+// k_sort_long_runs.
+__global__ void __launch_bounds__(kRunBlock)
+    k_sort_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift, uint64_t chunk,
+                unsigned long long *mid, uint64_t mid_cap, uint32_t *mid_n,
+                unsigned long long *lng, uint64_t lng_cap, uint32_t *lng_n,
+                unsigned int *fallback) {
+  __shared__ uint32_t s_mid, s_lng;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  // (the loop bound is the block's, so every lane takes part in the ballots)
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+  if (threadIdx.x == 0) {
+    s_mid = 0u;
+    s_lng = 0u;
+  }
+  __syncthreads();
+  const uint64_t c0 = (uint64_t)blockIdx.x * chunk, c1 = min(n, c0 + chunk);
+  unsigned long long *my_mid = mid + (uint64_t)blockIdx.x * mid_cap;
+  unsigned long long *my_lng = lng + (uint64_t)blockIdx.x * lng_cap;
+  // (the loop bound is the CTA's, so every lane takes part in the ballots)
+  for (uint64_t base = c0; base < c1; base += kRunBlock) {
     const uint64_t i = base + threadIdx.x;
-    uint64_t L = 0;
-    if (i < n) {
-      const uint64_t p = keys[i] >> pshift;
-      if (i == 0 || (keys[i - 1] >> pshift) != p) {  // a run's first position
-        L = 1;
-        while (i + L < n && L <= kWarpRun && (keys[i + L] >> pshift) == p) ++L;
+    const bool in = i < n;
+    const unsigned long long key = in ? keys[i] : 0ull;
+    const uint64_t p = key >> pshift;
+    uint64_t pp = __shfl_up_sync(0xffffffffu, p, 1);
+    if (lane == 0) pp = (in && i > 0) ? (keys[i - 1] >> pshift) : ~p;
+    const bool bnd = in && (i == 0 || pp != p);  // a run starts here
+    const unsigned bmask = __ballot_sync(0xffffffffu, bnd);
+    uint32_t L = 0;
+    if (bnd && i < c1) {  // a run of this chunk
+      const unsigned above = bmask & ~((2u << lane) - 1u);
+      if (above) {
+        L = (uint32_t)(__ffs((int)above) - 1 - lane);
+      } else {  // the warp's last run: it may go on past the warp
+        L = (uint32_t)min((uint64_t)(32 - lane), n - i);
+        while (i + L < n && L <= (uint32_t)kWarpRun && (keys[i + L] >> pshift) == p) ++L;
       }
     }
-    // longer runs are listed: one atomic per warp and list
-    const bool want_mid = L > kShortRun && L <= kWarpRun, want_lng = L > kWarpRun;
+    const bool want_mid = L > (uint32_t)kShortRun && L <= (uint32_t)kWarpRun;
+    const bool want_lng = L > (uint32_t)kWarpRun;
     const unsigned mm = __ballot_sync(0xffffffffu, want_mid);
     const unsigned lm = __ballot_sync(0xffffffffu, want_lng);
-    unsigned long long mb = 0, lb = 0;
+    uint32_t mb = 0, lb = 0;
     if (lane == 0) {
-      if (mm) mb = atomicAdd(mid_n, (unsigned long long)__popc(mm));
-      if (lm) lb = atomicAdd(lng_n, (unsigned long long)__popc(lm));
+      if (mm) mb = atomicAdd(&s_mid, (uint32_t)__popc(mm));
+      if (lm) lb = atomicAdd(&s_lng, (uint32_t)__popc(lm));
     }
     mb = __shfl_sync(0xffffffffu, mb, 0);
     lb = __shfl_sync(0xffffffffu, lb, 0);
-    if (want_mid || want_lng) {
-      const unsigned long long at = want_mid ? mb + __popc(mm & lt) : lb + __popc(lm & lt);
-      if (at < (want_mid ? mid_cap : lng_cap))
-        (want_mid ? mid : lng)[at] = i;
+    if (want_mid) {
+      const uint64_t at = (uint64_t)mb + __popc(mm & lt);
+      if (at < mid_cap)
+        my_mid[at] = i;
       else
         atomicExch(fallback, 1u);
     }
-    if (L < 2 || L > kShortRun) continue;
+    if (want_lng) {
+      const uint64_t at = (uint64_t)lb + __popc(lm & lt);
+      if (at < lng_cap)
+        my_lng[at] = i;
+      else
+        atomicExch(fallback, 1u);
+    }
+    if (L < 2 || L > (uint32_t)kShortRun) continue;
     unsigned long long rk[kShortRun];
-    uint4 rc[kShortRun];
+    bool ordered = true;
 #pragma unroll
     for (int a = 0; a < kShortRun; ++a) {
-      rk[a] = a < (int)L ? keys[i + a] : ~0ull;
-      rc[a] = a < (int)L ? counts[i + a] : make_uint4(0u, 0u, 0u, 0u);
+      rk[a] = a == 0 ? key : (a < (int)L ? keys[i + a] : ~0ull);
+      if (a > 0 && rk[a] < rk[a - 1]) ordered = false;  // (padding keys of all ones stay last)
     }
-    // a sorting network over the four places (padding keys of all ones stay last)
+    if (ordered) continue;
+    uint4 rc[kShortRun];
+#pragma unroll
+    for (int a = 0; a < kShortRun; ++a)
+      rc[a] = a < (int)L ? counts[i + a] : make_uint4(0u, 0u, 0u, 0u);
+    // a sorting network over the four places
 #define DBG_CSWAP(x, y)                        \
   if (rk[y] < rk[x]) {                         \
     const unsigned long long tk = rk[x];       \
@@ -228,19 +288,24 @@ __global__ void k_sort_runs(unsigned long long *keys, uint4 *counts, uint64_t n,
       }
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mid_n[blockIdx.x] = (uint32_t)min((uint64_t)s_mid, mid_cap);
+    lng_n[blockIdx.x] = (uint32_t)min((uint64_t)s_lng, lng_cap);
+  }
 }
 
-// A warp per listed run of kShortRun + 1 .. kWarpRun keys: lane a holds key
-// a (padding lanes all ones), a bitonic sort over the warp's registers
-// carries each key's lane of origin, and every lane then takes its counter
-// row from that lane.
-__global__ void k_sort_warp_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift,
-                                 const unsigned long long *list, const unsigned long long *list_n) {
+// A warp per listed run of kShortRun + 1 .. kWarpRun keys (CTA b takes the
+// runs of chunk b): lane a holds key a (padding lanes all ones), a bitonic
+// sort over the warp's registers carries each key's lane of origin, and
+// every lane then takes its counter row from that lane.
+__global__ void __launch_bounds__(kRunBlock)
+    k_sort_warp_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift,
+                     const unsigned long long *mid, uint64_t mid_cap, const uint32_t *mid_n) {
   const int lane = threadIdx.x & 31;
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const uint64_t runs = *list_n;
-  for (uint64_t r = (((uint64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; r < runs;
-       r += warps) {
+  const uint32_t runs = mid_n[blockIdx.x];
+  const unsigned long long *list = mid + (uint64_t)blockIdx.x * mid_cap;
+  for (uint32_t r = threadIdx.x >> 5; r < runs; r += kRunBlock / 32) {
     const uint64_t i = list[r];
     const uint64_t p = keys[i] >> pshift;
     const bool in = i + lane < n && (keys[i + lane] >> pshift) == p;
@@ -274,65 +339,70 @@ __global__ void k_sort_warp_runs(unsigned long long *keys, uint4 *counts, uint64
   }
 }
 
-// A CTA per listed run: its keys and positions sorted in shared memory
-// (bitonic, padded to a power of two with keys of all ones), then the keys
-// and counter rows written back in that order.
+// A CTA per listed run of more than kWarpRun keys (CTAs take the chunks' list
+// segments in turn): its keys and positions sorted in shared memory (bitonic,
+// padded to a power of two with keys of all ones), then the keys and counter
+// rows written back in that order.  A run longer than kMaxLongRun sets
+// *fallback.
 __global__ void __launch_bounds__(kLongBlock)
     k_sort_long_runs(unsigned long long *keys, uint4 *counts, uint64_t n, int pshift,
-                     const unsigned long long *list, const unsigned long long *list_n,
-                     unsigned int *fallback) {
+                     const unsigned long long *lng, uint64_t lng_cap, const uint32_t *lng_n,
+                     int chunks, unsigned int *fallback) {
   __shared__ unsigned long long s_key[kMaxLongRun];
   __shared__ uint16_t s_pos[kMaxLongRun];
   __shared__ uint4 s_row[kMaxLongRun];
   __shared__ uint32_t s_len;
-  const uint64_t runs = *list_n;
-  for (uint64_t r = blockIdx.x; r < runs; r += gridDim.x) {
-    const uint64_t i = list[r];
-    const uint64_t p = keys[i] >> pshift;
-    if (threadIdx.x == 0) {
-      uint64_t L = kWarpRun;  // (longer than that: it was listed)
-      while (i + L < n && L <= kMaxLongRun && (keys[i + L] >> pshift) == p) ++L;
-      s_len = (uint32_t)L;
-      if (L > kMaxLongRun) atomicExch(fallback, 1u);
-    }
-    __syncthreads();
-    const uint32_t L = s_len;
-    if (L > kMaxLongRun) {
+  for (int b = blockIdx.x; b < chunks; b += gridDim.x) {
+    const uint32_t runs = lng_n[b];
+    const unsigned long long *list = lng + (uint64_t)b * lng_cap;
+    for (uint32_t r = 0; r < runs; ++r) {
+      const uint64_t i = list[r];
+      const uint64_t p = keys[i] >> pshift;
+      if (threadIdx.x == 0) {
+        uint64_t L = kWarpRun;  // (longer than that: it was listed)
+        while (i + L < n && L <= kMaxLongRun && (keys[i + L] >> pshift) == p) ++L;
+        s_len = (uint32_t)L;
+        if (L > kMaxLongRun) atomicExch(fallback, 1u);
+      }
       __syncthreads();
-      continue;
-    }
-    uint32_t P = 1;
-    while (P < L) P <<= 1;
-    for (uint32_t j = threadIdx.x; j < P; j += kLongBlock) {
-      s_key[j] = j < L ? keys[i + j] : ~0ull;
-      s_pos[j] = (uint16_t)j;
-      if (j < L) s_row[j] = counts[i + j];
-    }
-    __syncthreads();
-    for (uint32_t size = 2; size <= P; size <<= 1) {
-      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t j = threadIdx.x; j < P; j += kLongBlock) {
-          const uint32_t o = j ^ stride;
-          if (o > j) {
-            const bool up = (j & size) == 0;
-            const unsigned long long a = s_key[j], b = s_key[o];
-            if ((a > b) == up) {
-              s_key[j] = b;
-              s_key[o] = a;
-              const uint16_t t = s_pos[j];
-              s_pos[j] = s_pos[o];
-              s_pos[o] = t;
+      const uint32_t L = s_len;
+      if (L > kMaxLongRun) {
+        __syncthreads();
+        continue;
+      }
+      uint32_t P = 1;
+      while (P < L) P <<= 1;
+      for (uint32_t j = threadIdx.x; j < P; j += kLongBlock) {
+        s_key[j] = j < L ? keys[i + j] : ~0ull;
+        s_pos[j] = (uint16_t)j;
+        if (j < L) s_row[j] = counts[i + j];
+      }
+      __syncthreads();
+      for (uint32_t size = 2; size <= P; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t j = threadIdx.x; j < P; j += kLongBlock) {
+            const uint32_t o = j ^ stride;
+            if (o > j) {
+              const bool up = (j & size) == 0;
+              const unsigned long long a = s_key[j], c = s_key[o];
+              if ((a > c) == up) {
+                s_key[j] = c;
+                s_key[o] = a;
+                const uint16_t t = s_pos[j];
+                s_pos[j] = s_pos[o];
+                s_pos[o] = t;
+              }
             }
           }
+          __syncthreads();
         }
-        __syncthreads();
       }
+      for (uint32_t j = threadIdx.x; j < L; j += kLongBlock) {
+        keys[i + j] = s_key[j];
+        counts[i + j] = s_row[s_pos[j]];
+      }
+      __syncthreads();
     }
-    for (uint32_t j = threadIdx.x; j < L; j += kLongBlock) {
-      keys[i + j] = s_key[j];
-      counts[i + j] = s_row[s_pos[j]];
-    }
-    __syncthreads();
   }
 }
 
@@ -489,84 +559,131 @@ int export_pairs(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts_
   return rc;
 }
 
+// Scratch of the prefix-sort export: [count, flag][run list counts][sort
+// temp][sorted indices][run lists], and without in-place outputs [prefix a]
+// [index a][prefix b][index b][keys][counters].
+struct PrefixScratch {
+  size_t temp, head, wb, lists, total;
+};
+
+int prefix_scratch(int k, uint64_t D, bool in_place, PrefixScratch &ps) {
+  const int bits = 2 * (k - 1);
+  size_t temp = 0;
+  cub::DoubleBuffer<uint32_t> dk(nullptr, nullptr), dv(nullptr, nullptr);
+  DBG_CK(cub::DeviceRadixSort::SortPairs(nullptr, temp, dk, dv, (int64_t)D, 0,
+                                         bits > 32 ? 32 : bits, (cudaStream_t)0));
+  ps.temp = temp;
+  ps.head = 256 + align256(2 * (size_t)kRunCtas * sizeof(uint32_t)) + align256(temp);
+  ps.wb = align256(D * sizeof(uint32_t));
+  ps.lists = align256(run_lists(D).bytes());
+  ps.total = ps.head + ps.wb + ps.lists +
+             (in_place ? 0 : 4 * ps.wb + align256(D * 8) + align256(D * sizeof(uint4)));
+  return DBG_OK;
+}
+
+bool in_place_outputs(const uint64_t *keys_out, const uint32_t *counts_out) {
+  return is_device_ptr(keys_out) && is_device_ptr(counts_out) &&
+         ((uintptr_t)keys_out & 15u) == 0 && ((uintptr_t)counts_out & 15u) == 0;
+}
+
+// Compaction of the prefix export into in-place outputs of `stride` rows,
+// counting the occupied slots as it goes (no separate counting pass): at most
+// `stride` (prefix, index) pairs are written -- prefixes at keys_out as 32-bit
+// words, indices after them -- and *D_out receives the count.  Returns the
+// sticky status (or NEEDS_GROW) instead when the graph has one.
+int compact_counted(dbg_handle h, uint64_t *keys_out, uint64_t stride, uint64_t *D_out,
+                    cudaStream_t s) {
+  const int bits = 2 * (h->k - 1);
+  const int pshift = bits > 32 ? bits - 32 : 0;
+  uint32_t *pa = reinterpret_cast<uint32_t *>(keys_out);
+  DBG_CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long), s));
+  const int sms = std::max(1, h->sm_count);
+  k_compact_prefix<<<sms * 8, kCompactBlock, 0, s>>>(h->table, h->n_slots, pshift, pa, pa + stride,
+                                                     h->d_acc, stride);
+  DBG_CK(cudaGetLastError());
+  unsigned long long D = 0, spilled = 0;
+  uint32_t status = 0;
+  DBG_CK(cudaMemcpyAsync(&D, h->d_acc, sizeof(D), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaMemcpyAsync(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaMemcpyAsync(&spilled, h->d_spill_count, sizeof(spilled), cudaMemcpyDeviceToHost, s));
+  DBG_CK(cudaStreamSynchronize(s));
+  if (status != DBG_OK) return (int)status;
+  if (spilled > 0) return DBG_ERR_NEEDS_GROW;
+  *D_out = D;
+  return DBG_OK;
+}
+
 // The prefix-sort export of D vertices (tables of at most 2^32 slots).
 // Buffers: two (prefix, index) pairs for the sort, the sorted indices, the
-// sort's temporary space, a counter and the long-run flag.  In place (both
-// outputs 16-byte aligned device buffers) the pairs live in keys_out (8
-// bytes a vertex) and counts_out, and the gather writes the outputs
-// directly; otherwise everything is temporary.  Returns DBG_ERR_CAPACITY
-// (not a graph error: the caller falls back to the full-width sort) when a
-// run of equal prefixes is too long.
+// sort's temporary space, a counter, the long-run flag and the run lists.  In
+// place (both outputs 16-byte aligned device buffers) the pairs live in
+// keys_out (8 bytes a row) and counts_out, and the gather writes the outputs
+// directly; otherwise everything is temporary.  `stride` (in place): the rows
+// the pair layout assumes (D when 0); `compacted`: compact_counted has
+// already written the pairs with that stride.  Returns DBG_ERR_CAPACITY (not
+// a graph error: the caller falls back to the full-width sort) when a run of
+// equal prefixes is too long.
 int export_prefix(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts_out,
-                  cudaStream_t s, void *caller, uint64_t caller_bytes) {
+                  cudaStream_t s, void *caller, uint64_t caller_bytes, uint64_t stride = 0,
+                  bool compacted = false) {
   const int bits = 2 * (h->k - 1);
   const int pshift = bits > 32 ? bits - 32 : 0;
   const int pbits = bits > 32 ? 32 : bits;
-  const bool in_place = is_device_ptr(keys_out) && is_device_ptr(counts_out) &&
-                        ((uintptr_t)keys_out & 15u) == 0 && ((uintptr_t)counts_out & 15u) == 0;
-  if (caller && !in_place) return DBG_ERR_INVALID_ARG;
-  size_t temp_bytes = 0;
-  {
-    cub::DoubleBuffer<uint32_t> dk(nullptr, nullptr), dv(nullptr, nullptr);
-    DBG_CK(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, dk, dv, (int64_t)D, 0, pbits, s));
-  }
-  const size_t wb = align256(D * sizeof(uint32_t));
-  const uint64_t mid_cap = D / (kShortRun + 1) + 1;  // runs longer than kShortRun, at most
-  const uint64_t list_cap = D / (kWarpRun + 1) + 1;   // runs longer than kWarpRun, at most
-  // scratch: [count, flag, list count][sort temp][sorted indices][long runs],
-  // and without in-place outputs [prefix a][index a][prefix b][index b][keys]
-  // [counters]
-  const size_t head = 256 + align256(temp_bytes);
-  const size_t lb = align256(list_cap * 8) + align256(mid_cap * 8);
-  const size_t total = head + wb + lb +
-                       (in_place ? 0 : 4 * wb + align256(D * 8) + align256(D * sizeof(uint4)));
+  const bool in_place = in_place_outputs(keys_out, counts_out);
+  if ((caller || compacted) && !in_place) return DBG_ERR_INVALID_ARG;
+  if (stride == 0) stride = D;
+  PrefixScratch ps;
+  DBG_TRY(prefix_scratch(h->k, D, in_place, ps));
+  const RunLists rl = run_lists(D);
   char *buf = nullptr;
   if (caller) {
-    if (caller_bytes < total || ((uintptr_t)caller & 255u)) return DBG_ERR_INVALID_ARG;
+    if (caller_bytes < ps.total || ((uintptr_t)caller & 255u)) return DBG_ERR_INVALID_ARG;
     buf = static_cast<char *>(caller);
   } else {
-    DBG_TRY(scratch_alloc(reinterpret_cast<void **>(&buf), total, s));
+    DBG_TRY(scratch_alloc(reinterpret_cast<void **>(&buf), ps.total, s));
   }
   unsigned long long *count = reinterpret_cast<unsigned long long *>(buf);
   unsigned int *fallback = reinterpret_cast<unsigned int *>(buf + 8);
-  unsigned long long *list_n = reinterpret_cast<unsigned long long *>(buf + 16);
-  unsigned long long *mid_n = reinterpret_cast<unsigned long long *>(buf + 24);
-  void *temp = buf + 256;
-  uint32_t *idx_final = reinterpret_cast<uint32_t *>(buf + head);
-  unsigned long long *list = reinterpret_cast<unsigned long long *>(buf + head + wb);
-  unsigned long long *mid = list + align256(list_cap * 8) / 8;
+  uint32_t *mid_n = reinterpret_cast<uint32_t *>(buf + 256);
+  uint32_t *lng_n = mid_n + kRunCtas;
+  void *temp = buf + ps.head - align256(ps.temp);
+  uint32_t *idx_final = reinterpret_cast<uint32_t *>(buf + ps.head);
+  unsigned long long *mid = reinterpret_cast<unsigned long long *>(buf + ps.head + ps.wb);
+  unsigned long long *lng = mid + (uint64_t)rl.ctas * rl.mid_cap;
   uint32_t *pa, *ia, *pb, *ib;
   unsigned long long *keys;
   uint4 *counts;
   if (in_place) {
-    char *kb = reinterpret_cast<char *>(keys_out), *cb = reinterpret_cast<char *>(counts_out);
-    pa = reinterpret_cast<uint32_t *>(kb);
-    ia = reinterpret_cast<uint32_t *>(kb + 4 * D);
-    pb = reinterpret_cast<uint32_t *>(cb);
-    ib = reinterpret_cast<uint32_t *>(cb + 4 * D);
+    pa = reinterpret_cast<uint32_t *>(keys_out);
+    ia = pa + stride;
+    pb = reinterpret_cast<uint32_t *>(counts_out);
+    ib = pb + stride;
     keys = reinterpret_cast<unsigned long long *>(keys_out);
     counts = reinterpret_cast<uint4 *>(counts_out);
   } else {
-    char *p = buf + head + wb + lb;
+    char *p = buf + ps.head + ps.wb + ps.lists;
     pa = reinterpret_cast<uint32_t *>(p);
-    ia = reinterpret_cast<uint32_t *>(p + wb);
-    pb = reinterpret_cast<uint32_t *>(p + 2 * wb);
-    ib = reinterpret_cast<uint32_t *>(p + 3 * wb);
-    keys = reinterpret_cast<unsigned long long *>(p + 4 * wb);
-    counts = reinterpret_cast<uint4 *>(p + 4 * wb + align256(D * 8));
+    ia = reinterpret_cast<uint32_t *>(p + ps.wb);
+    pb = reinterpret_cast<uint32_t *>(p + 2 * ps.wb);
+    ib = reinterpret_cast<uint32_t *>(p + 3 * ps.wb);
+    keys = reinterpret_cast<unsigned long long *>(p + 4 * ps.wb);
+    counts = reinterpret_cast<uint4 *>(p + 4 * ps.wb + align256(D * 8));
   }
 
   int rc = DBG_OK;
   unsigned int fallback_host = 0;
   do {
-    cudaError_t e = cudaMemsetAsync(buf, 0, 32, s);  // count, flag, list counts
+    cudaError_t e = cudaMemsetAsync(buf, 0, 16, s);  // count, flag
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync"); break; }
     const int sms = std::max(1, h->sm_count);
-    k_compact_prefix<<<sms * 8, kCompactBlock, 0, s>>>(h->table, h->n_slots, pshift, pa, ia, count,
-                                                       D);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { rc = cuda_fail(e, "k_compact_prefix"); break; }
+    if (!compacted) {
+      k_compact_prefix<<<sms * 8, kCompactBlock, 0, s>>>(h->table, h->n_slots, pshift, pa, ia,
+                                                         count, D);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) { rc = cuda_fail(e, "k_compact_prefix"); break; }
+    }
     cub::DoubleBuffer<uint32_t> dk(pa, pb), dv(ia, ib);
+    size_t temp_bytes = ps.temp;
     e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, dk, dv, (int64_t)D, 0, pbits, s);
     if (e != cudaSuccess) { rc = cuda_fail(e, "DeviceRadixSort::SortPairs"); break; }
     // the gather overwrites the buffers the sorted indices sit in: move them out
@@ -576,15 +693,16 @@ int export_prefix(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts
     e = cudaGetLastError();
     if (e != cudaSuccess) { rc = cuda_fail(e, "k_gather_slots"); break; }
     if (pshift > 0) {  // the runs of equal prefixes, in key order
-      k_sort_runs<<<sms * 8, 256, 0, s>>>(keys, counts, D, pshift, mid, mid_n, mid_cap, list,
-                                          list_n, list_cap, fallback);
+      k_sort_runs<<<rl.ctas, kRunBlock, 0, s>>>(keys, counts, D, pshift, rl.chunk, mid, rl.mid_cap,
+                                                mid_n, lng, rl.lng_cap, lng_n, fallback);
       e = cudaGetLastError();
       if (e != cudaSuccess) { rc = cuda_fail(e, "k_sort_runs"); break; }
-      k_sort_warp_runs<<<sms * 8, 256, 0, s>>>(keys, counts, D, pshift, mid, mid_n);
+      k_sort_warp_runs<<<rl.ctas, kRunBlock, 0, s>>>(keys, counts, D, pshift, mid, rl.mid_cap,
+                                                     mid_n);
       e = cudaGetLastError();
       if (e != cudaSuccess) { rc = cuda_fail(e, "k_sort_warp_runs"); break; }
-      k_sort_long_runs<<<sms * 4, kLongBlock, 0, s>>>(keys, counts, D, pshift, list, list_n,
-                                                      fallback);
+      k_sort_long_runs<<<std::min(rl.ctas, sms * 4), kLongBlock, 0, s>>>(
+          keys, counts, D, pshift, lng, rl.lng_cap, lng_n, rl.ctas, fallback);
       e = cudaGetLastError();
       if (e != cudaSuccess) { rc = cuda_fail(e, "k_sort_long_runs"); break; }
       e = cudaMemcpyAsync(&fallback_host, fallback, sizeof(fallback_host), cudaMemcpyDeviceToHost,
@@ -613,13 +731,9 @@ int export_prefix(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts
 
 // Scratch of an in-place prefix export (see export_prefix).
 int prefix_scratch_bytes(int k, uint64_t D, uint64_t &bytes) {
-  const int bits = 2 * (k - 1);
-  size_t temp = 0;
-  cub::DoubleBuffer<uint32_t> dk(nullptr, nullptr), dv(nullptr, nullptr);
-  DBG_CK(cub::DeviceRadixSort::SortPairs(nullptr, temp, dk, dv, (int64_t)D, 0,
-                                         bits > 32 ? 32 : bits, (cudaStream_t)0));
-  bytes = 256 + align256(temp) + align256(D * sizeof(uint32_t)) +
-          align256((D / (kWarpRun + 1) + 1) * 8) + align256((D / (kShortRun + 1) + 1) * 8);
+  PrefixScratch ps;
+  DBG_TRY(prefix_scratch(k, D, true, ps));
+  bytes = ps.total;
   return DBG_OK;
 }
 
@@ -635,7 +749,20 @@ extern "C" int dbg_export_sorted(dbg_handle h, uint64_t *keys_out, uint32_t *cou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   uint64_t D = 0;
-  int st = dbg_stats(h, &D, nullptr, stream);
+  int st;
+  if (h->k <= 32 && h->n_slots <= 0xFFFFFFFFull && max_n > 0 &&
+      in_place_outputs(keys_out, counts_out)) {
+    // in place: the compaction into the outputs counts the vertices itself
+    st = compact_counted(h, keys_out, max_n, &D, s);
+    if (st != DBG_OK) return st;
+    *n_out = D;
+    if (D > max_n) return DBG_ERR_BUFFER_TOO_SMALL;
+    if (D == 0) return DBG_OK;
+    st = export_prefix(h, D, keys_out, counts_out, s, nullptr, 0, max_n, true);
+    if (st != DBG_ERR_CAPACITY) return st;  // (a long run of equal prefixes: full width)
+    return export_pairs<uint32_t>(h, D, keys_out, counts_out, s);
+  }
+  st = dbg_stats(h, &D, nullptr, stream);
   if (st != DBG_OK) return st;
   *n_out = D;
   if (D > max_n) return DBG_ERR_BUFFER_TOO_SMALL;
@@ -666,15 +793,17 @@ extern "C" int dbg_export_sorted_with(dbg_handle h, uint64_t *keys_out, uint32_t
   if (!h || !n_out || h->k > 32 || h->n_slots > 0xFFFFFFFFull) return DBG_ERR_INVALID_ARG;
   Guard g(h->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint64_t D = 0;
-  int st = dbg_stats(h, &D, nullptr, stream);
+  const bool counted = max_n > 0 && scratch && in_place_outputs(keys_out, counts_out);
+  int st = counted ? compact_counted(h, keys_out, max_n, &D, s) : dbg_stats(h, &D, nullptr, stream);
   if (st != DBG_OK) return st;
   *n_out = D;
   if (D > max_n) return DBG_ERR_BUFFER_TOO_SMALL;
   if (D == 0) return DBG_OK;
   if (!keys_out || !counts_out || !scratch) return DBG_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = export_prefix(h, D, keys_out, counts_out, s, scratch, scratch_bytes);
+  st = export_prefix(h, D, keys_out, counts_out, s, scratch, scratch_bytes, counted ? max_n : 0,
+                     counted);
   if (st != DBG_ERR_CAPACITY) return st;  // (a long run of equal prefixes: full width)
   return export_pairs<uint32_t>(h, D, keys_out, counts_out, s, scratch, scratch_bytes);
 }

@@ -237,12 +237,13 @@ def test_export_with_caller_scratch():
     g.close()
 
 
-@pytest.mark.parametrize("n_shared", [20, 200])
+@pytest.mark.parametrize("n_shared", [20, 200, 2100])
 def test_export_keys_sharing_a_prefix(n_shared):
     # keys of k = 31 are sorted by their top 32 bits (16 bases) first; reads
-    # whose first 16 bases agree give runs of keys with one prefix: 20 of them
-    # are put in order inside the run, 200 (a run over 32) make the export
-    # fall back to the full-width sort -- the same graph either way
+    # whose first 16 bases agree give runs of keys with one prefix: a run of
+    # 20 is put in order by a warp, one of 200 by a CTA in shared memory, and
+    # one of 2100 (over 2048) makes the export fall back to the full-width
+    # sort -- the same graph every way
     import torch
     rng = np.random.default_rng(n_shared)
     head = "ACGTTGCAAGGCTTAA"
@@ -255,4 +256,32 @@ def test_export_keys_sharing_a_prefix(n_shared):
     keys, counts = g.export_device()    # device outputs: the sort runs inside them
     assert_same_graph((keys.cpu().numpy().view(np.uint64), counts.cpu().numpy().view(np.uint32)),
                       exp)
+    g.close()
+
+
+def test_export_into_larger_and_smaller_device_buffers():
+    # the in-place export lays its sort out over all max_n rows of the
+    # outputs and counts the vertices while it compacts: rows beyond D are
+    # scratch, and too few rows give BUFFER_TOO_SMALL with the count
+    import ctypes
+
+    import torch
+    rs = synth.ragged_reads(2500, 220, 31, 4600, lead=1)
+    g = gpu_graph(rs)
+    exp = oracle_export(rs)
+    D = exp[0].size
+    lib = dbg.load()
+    for rows in (D, D + 1, 3 * D + 7):
+        keys = torch.empty(rows, dtype=torch.int64, device="cuda")
+        counts = torch.empty((rows, 4), dtype=torch.int32, device="cuda")
+        assert g.export_into(keys, counts) == D
+        assert_same_graph((keys[:D].cpu().numpy().view(np.uint64),
+                           counts[:D].cpu().numpy().view(np.uint32)), exp)
+    keys = torch.empty(D - 1, dtype=torch.int64, device="cuda")
+    counts = torch.empty((D - 1, 4), dtype=torch.int32, device="cuda")
+    n = ctypes.c_uint64()
+    st = lib.dbg_export_sorted(g.handle, keys.data_ptr(), counts.data_ptr(), D - 1, ctypes.byref(n),
+                               None)
+    assert st == dbg.ERR_BUFFER_TOO_SMALL and n.value == D
+    assert g.stats()[0] == D  # the graph is untouched
     g.close()
