@@ -21,40 +21,55 @@ namespace {
 
 constexpr unsigned long long kSketchSalt = 0x9E3779B97F4A7C15ull;
 constexpr int kSketchRegs = DBG_SKETCH_REGISTERS;
-constexpr int kSketchRun = 16;  // positions of one read per thread and round (no visitor state)
-
-__device__ __forceinline__ void sketch_hash(uint64_t key, uint32_t &idx, uint32_t &rho) {
-  const uint64_t h = fmix64(key ^ kSketchSalt);
-  idx = (uint32_t)(h >> 54);
-  const uint64_t rest = h << 10;
-  rho = rest ? (uint32_t)__clzll(rest) + 1u : 55u;
-}
+constexpr int kSketchRun = 16;  // positions of one read per thread and round
+constexpr int kSketchCtas = 7;  // CTAs of 256 threads per SM (shared memory allows 7)
 
 // Registers in shared memory (one read set per launch).  A register only
-// grows, and after the first few thousand keys almost no key raises it, so
-// each key reads its register first and takes the atomic only to raise it.
+// grows, and after the first few thousand keys almost no key raises it: a key
+// whose rho cannot exceed the smallest register (a lower bound the CTA
+// refreshes at every tile start) is dropped after one compare, the others
+// read their register first and take the atomic only to raise it.  The
+// registers are the same as without the bound.
 struct SketchVisitor {
   static constexpr bool kUniformRounds = false;
   uint32_t *s_reg;
-  __device__ void tile_begin() {}
+  volatile uint32_t *s_floor;  // every register is at least this (any value it held stays true)
+  uint64_t lim = ~0ull;        // rest >= lim  <=>  rho <= floor (~0: none)
+  __device__ void tile_begin() {
+    const uint32_t f = *s_floor;
+    lim = f == 0u ? ~0ull : (f >= 54u ? 1024ull : 1ull << (64u - f));
+    if (threadIdx.x < 32) {  // the next tile's bound
+      uint32_t m = ~0u;
+      for (int j = threadIdx.x; j < kSketchRegs; j += 32)
+        m = min(m, *reinterpret_cast<volatile uint32_t *>(&s_reg[j]));
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, d));
+      if (threadIdx.x == 0) *s_floor = m;
+    }
+  }
   __device__ bool stop(int) { return false; }
   __device__ void round_end() {}
   __device__ void vertex(bool valid, uint64_t key, bool, uint32_t, int, int, const VertexCtx &) {
     if (!valid) return;
-    uint32_t idx, rho;
-    sketch_hash(key, idx, rho);
+    const uint64_t h = fmix64(key ^ kSketchSalt);
+    const uint64_t rest = h << 10;
+    if (rest >= lim) return;  // 1 + clz(rest) <= floor: no register can rise
+    const uint32_t idx = (uint32_t)(h >> 54);
+    const uint32_t rho = rest ? (uint32_t)__clzll(rest) + 1u : 55u;
     if (rho > *reinterpret_cast<volatile uint32_t *>(&s_reg[idx])) atomicMax(&s_reg[idx], rho);
   }
 };
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, kSketchCtas)
     k_sketch(const __grid_constant__ ItemPack<1> pk, int tile_reads, uint32_t *regs) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *s_reg = reinterpret_cast<uint32_t *>(smem + tile_smem_bytes(tile_reads));
+  __shared__ uint32_t s_floor;
   for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK) s_reg[j] = 0u;
+  if (threadIdx.x == 0) s_floor = 0u;
   __syncthreads();
-  SketchVisitor vis{s_reg};
+  SketchVisitor vis{s_reg, &s_floor};
   for_each_vertex<BLOCK, 1, kSketchRun>(pk, tile_reads, smem, vis, blockIdx.x, pk.total_tiles,
                                         gridDim.x);
   __syncthreads();
@@ -67,14 +82,16 @@ __global__ void __launch_bounds__(BLOCK)
 // item at hand and merges them into that item's global registers (carried in
 // the descriptor's table pointer) when its tiles of the item end.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, kSketchCtas)
     k_sketch_batch(const __grid_constant__ ItemPack<kBatchItems> pk, int tile_reads,
                    uint64_t chunk) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *s_reg = reinterpret_cast<uint32_t *>(smem + tile_smem_bytes(tile_reads));
+  __shared__ uint32_t s_floor;
   for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK) s_reg[j] = 0u;
+  if (threadIdx.x == 0) s_floor = 0u;
   __syncthreads();
-  SketchVisitor vis{s_reg};
+  SketchVisitor vis{s_reg, &s_floor};
   const uint64_t t1 = min(pk.total_tiles, (blockIdx.x + 1) * chunk);
   for (uint64_t t = blockIdx.x * chunk; t < t1;) {
     const int it = find_item(pk, t);
@@ -88,6 +105,7 @@ __global__ void __launch_bounds__(BLOCK)
         atomicMax(&g[j], s_reg[j]);
         s_reg[j] = 0u;
       }
+    if (threadIdx.x == 0) s_floor = 0u;  // the next item starts from empty registers
     __syncthreads();
     t = tb;
   }
