@@ -55,7 +55,7 @@ def test_committed_traffic_record_is_well_formed():
     # code it was taken on, and an ncu command that leaves the clocks alone
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "insert_traffic.json")))
     for wl, kernels in rec.items():
-        assert wl in ("100mbp_30x_k31", "5mbp_50x_k31")
+        assert wl in ("100mbp_30x_k31", "5mbp_50x_k31", "2mbp_30x_k31")
         for name, e in kernels.items():
             assert name in ("bin_count", "bin_scatter", "bin_split", "bin_apply", "bin_deferred")
             assert e["dram_bytes_per_launch"] > 0 and e["kernels"]
