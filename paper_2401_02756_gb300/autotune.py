@@ -48,9 +48,10 @@ def candidates(k: int, binned: bool) -> list[dict]:
 
 
 def batch_candidates() -> list[dict]:
-    """The settings tried for a batched build: the binned chains' shapes."""
-    return ([_tiled(0, 0, 0)] + [_tiled(r, 0, 0) for r in (19, 20)] +
-            [_tiled(0, sr, 0) for sr in (256, 512)] + [_tiled(0, 0, 1024)])
+    """The settings tried for a batched build: the binned chains' shapes --
+    region sizes with the split's block size, the scatter's read tile."""
+    return ([_tiled(0, 0, 0)] + [_tiled(r, 0, st) for r in (18, 19, 20) for st in (0, 512)] +
+            [_tiled(r, sr, 0) for r in (0, 19) for sr in (256, 512)] + [_tiled(0, 0, 1024)])
 
 
 def time_setting(graph: "dbg.Graph", packed, offsets, setting: dict, reps: int = 2,

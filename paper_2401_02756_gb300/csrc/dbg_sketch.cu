@@ -34,10 +34,13 @@ struct SketchVisitor {
   static constexpr bool kUniformRounds = false;
   uint32_t *s_reg;
   volatile uint32_t *s_floor;  // every register is at least this (any value it held stays true)
-  uint64_t lim = ~0ull;        // rest >= lim  <=>  rho <= floor (~0: none)
+  // a key whose rest (the hash's 54 low bits, left-aligned) has its high word
+  // above lim_hi has rho <= floor: rest >= 2^(64 - floor) for floor <= 32;
+  // for a floor above 32, rest >= 2^32 suffices; a floor of 0 drops nothing
+  uint32_t lim_hi = ~0u;
   __device__ void tile_begin() {
     const uint32_t f = *s_floor;
-    lim = f == 0u ? ~0ull : (f >= 54u ? 1024ull : 1ull << (64u - f));
+    lim_hi = f == 0u ? ~0u : (f <= 32u ? (1u << (32u - f)) - 1u : 0u);
     if (threadIdx.x < 32) {  // the next tile's bound
       uint32_t m = ~0u;
       for (int j = threadIdx.x; j < kSketchRegs; j += 32)
@@ -52,8 +55,9 @@ struct SketchVisitor {
   __device__ void vertex(bool valid, uint64_t key, bool, uint32_t, int, int, const VertexCtx &) {
     if (!valid) return;
     const uint64_t h = fmix64(key ^ kSketchSalt);
+    const uint32_t rest_hi = (uint32_t)(h >> 22);  // bits 53..22 of the hash
+    if (rest_hi > lim_hi) return;  // 1 + clz(rest) <= floor: no register can rise
     const uint64_t rest = h << 10;
-    if (rest >= lim) return;  // 1 + clz(rest) <= floor: no register can rise
     const uint32_t idx = (uint32_t)(h >> 54);
     const uint32_t rho = rest ? (uint32_t)__clzll(rest) + 1u : 55u;
     if (rho > *reinterpret_cast<volatile uint32_t *>(&s_reg[idx])) atomicMax(&s_reg[idx], rho);
