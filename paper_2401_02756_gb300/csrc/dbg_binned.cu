@@ -1017,11 +1017,34 @@ __device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
   return (x - 0x01010101u) & ~x & 0x80808080u;
 }
 
+// The tile in shared memory.  AosTile: the table's own 32-byte slots (a tile
+// brought in from the table by a bulk copy).  SoaTile (fresh tables, built
+// from EMPTY): the keys in one array and the counters label-major.  With
+// 32-byte slots every slot's key falls on one of four bank pairs, so a warp's
+// random slots conflict (41 % of the apply's shared-memory wavefronts were
+// conflicts); in the SoA tile the keys spread over 16 bank pairs and each
+// label's counters over all 32 banks.  The copy-out writes 32-byte slots.
+struct AosTile {
+  Slot *st;
+  __device__ unsigned long long *key(int sl) const { return &st[sl].key; }
+  __device__ uint32_t *counter(int sl, uint32_t label) const { return &st[sl].cnt[label]; }
+};
+struct SoaTile {
+  unsigned long long *keys;  // [kTileSlots]
+  uint32_t *counts;          // [4][kTileSlots]
+  __device__ unsigned long long *key(int sl) const { return &keys[sl]; }
+  __device__ uint32_t *counter(int sl, uint32_t label) const {
+    return &counts[label * (uint32_t)kTileSlots + (uint32_t)sl];
+  }
+};
+constexpr size_t kSoaTileBytes = (size_t)kTileSlots * (8 + 16);
+
 // One event against the tile in shared memory: found or claimed and counted,
 // failed (max_probes inside the tile), or deferred (the probe left the tile).
 // Slots are examined in probe order exactly as one at a time would: the first
 // slot from home that holds the key or is empty decides.
-__device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, uint64_t first,
+template <class Tile>
+__device__ __forceinline__ void tile_event(uint64_t e, const Tile &tile, uint8_t *fp, uint64_t first,
                                            int len, uint64_t n_slots, uint32_t max_probes,
                                            uint32_t *status, SpillRecord *spill,
                                            uint64_t spill_cap, unsigned long long *spill_count,
@@ -1051,11 +1074,11 @@ __device__ __forceinline__ void tile_event(uint64_t e, Slot *st, uint8_t *fp, ui
     // returns an occupied slot's key, so found, claimed and another key take
     // one path (measured faster than a load for the byte matches and a CAS
     // for the empty bytes, whose paths diverge)
-    const unsigned long long prev = atomicCAS(&st[sl].key, kEmpty, key);
+    const unsigned long long prev = atomicCAS(tile.key(sl), kEmpty, key);
     if (prev == kEmpty) fp[sl] = (uint8_t)f;
     const bool found = prev == kEmpty || prev == key;
     if (found) {
-      if (e & 4ull) atomicAdd(&st[sl].cnt[e & 3ull], 1u);
+      if (e & 4ull) atomicAdd(tile.counter(sl, (uint32_t)(e & 3ull)), 1u);
       return;
     }
     q = sl + 1;  // another key (claimed meanwhile, or a byte collision): on to the next
@@ -1092,10 +1115,9 @@ __global__ void k_tile_map(TileAux aux, int parts, const uint32_t *use_binned) {
 // is the tables' reset: the separate emptying pass (a full write of every
 // table) disappears.  Each thread copies out and then re-initialises the
 // same 16-byte words of the tile, so the next tile needs no extra barrier.
-__device__ __forceinline__ void empty_tile_words(uint4 *st4, uint32_t *fp32) {
-  const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);  // key EMPTY, cnt[0..1]
-  const uint4 tail = make_uint4(0u, 0u, 0u, 0u);                    // cnt[2..3], pad
-  for (int i = threadIdx.x; i < 2 * kTileSlots; i += blockDim.x) st4[i] = (i & 1) ? tail : head;
+__device__ __forceinline__ void empty_soa_tile(const SoaTile &tile, uint32_t *fp32) {
+  for (int i = threadIdx.x; i < kTileSlots; i += blockDim.x) tile.keys[i] = kEmpty;
+  for (int i = threadIdx.x; i < 4 * kTileSlots; i += blockDim.x) tile.counts[i] = 0u;
   for (int i = threadIdx.x; i < kFpBytes / 4; i += blockDim.x) fp32[i] = 0u;
 }
 
@@ -1106,14 +1128,17 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 thr
                  int tpr_log2, const uint32_t *use_binned) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   extern __shared__ __align__(16) unsigned char smem[];  // (bulk copies need 16 bytes)
-  Slot *st = reinterpret_cast<Slot *>(smem);                 // kTileSlots slots
-  uint8_t *fp = smem + (size_t)kTileSlots * sizeof(Slot);   // kFpBytes fingerprints
-  uint4 *st4 = reinterpret_cast<uint4 *>(smem);
+  // !FRESH: kTileSlots slots (AoS); FRESH: keys and label-major counters (SoA)
+  Slot *st = reinterpret_cast<Slot *>(smem);
+  const AosTile aos{st};
+  const SoaTile soa{reinterpret_cast<unsigned long long *>(smem),
+                    reinterpret_cast<uint32_t *>(smem + (size_t)kTileSlots * 8)};
+  uint8_t *fp = smem + (FRESH ? kSoaTileBytes : (size_t)kTileSlots * sizeof(Slot));  // kFpBytes
   uint32_t *fp32 = reinterpret_cast<uint32_t *>(fp);
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_stop, s_failed;
   if constexpr (FRESH) {
-    empty_tile_words(st4, fp32);
+    empty_soa_tile(soa, fp32);
   } else if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
@@ -1195,10 +1220,15 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 thr
     if (s_stop == 0u) {  // an earlier error stops the insert, as in the direct kernel
       for (uint64_t base = a;;) {
 #pragma unroll
-        for (int r = 0; r < kBatch; ++r)
-          if (e[r] != kEmpty)
-            tile_event(e[r], st, fp, first, len, n_slots, it.max_probes, status, it.spill,
+        for (int r = 0; r < kBatch; ++r) {
+          if (e[r] == kEmpty) continue;
+          if constexpr (FRESH)
+            tile_event(e[r], soa, fp, first, len, n_slots, it.max_probes, status, it.spill,
                        it.spill_cap, it.spill_count, p, ev, begin, aux.deferred_n);
+          else
+            tile_event(e[r], aos, fp, first, len, n_slots, it.max_probes, status, it.spill,
+                       it.spill_cap, it.spill_count, p, ev, begin, aux.deferred_n);
+        }
         base += (uint64_t)BLOCK * kBatch;
         if (base >= b) break;
         load_batch<BLOCK>(ev2, base, b, e);
@@ -1206,14 +1236,28 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 thr
     }
     __syncthreads();
     if constexpr (FRESH) {
-      // copy the tile out (written even after an earlier error: the table is
-      // at least empty there) and re-make the EMPTY tile, word by word
+      // copy the tile out as 32-byte slots (written even after an earlier
+      // error: the table is at least empty there), 16 bytes a thread: an even
+      // word is (key, cnt[0], cnt[1]), an odd one (cnt[2], cnt[3], pad).  Each
+      // thread re-makes the EMPTY words it has just read.  (Slots past `len`
+      // take no event: they stay EMPTY.)
       uint4 *dst = reinterpret_cast<uint4 *>(table + first);
-      const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
-      const uint4 tail = make_uint4(0u, 0u, 0u, 0u);
-      for (int i = threadIdx.x; i < 2 * kTileSlots; i += BLOCK) {
-        if (i < 2 * len) __stcs(dst + i, st4[i]);
-        st4[i] = (i & 1) ? tail : head;
+      const uint32_t K = (uint32_t)kTileSlots;
+      for (int i = threadIdx.x; i < 2 * len; i += BLOCK) {
+        const uint32_t sl = (uint32_t)i >> 1;
+        uint4 v;
+        if ((i & 1) == 0) {
+          const unsigned long long k = soa.keys[sl];
+          v = make_uint4((uint32_t)k, (uint32_t)(k >> 32), soa.counts[sl], soa.counts[K + sl]);
+          soa.keys[sl] = kEmpty;
+          soa.counts[sl] = 0u;
+          soa.counts[K + sl] = 0u;
+        } else {
+          v = make_uint4(soa.counts[2 * K + sl], soa.counts[3 * K + sl], 0u, 0u);
+          soa.counts[2 * K + sl] = 0u;
+          soa.counts[3 * K + sl] = 0u;
+        }
+        __stcs(dst + i, v);
       }
       for (int i = threadIdx.x; i < kFpBytes / 4; i += BLOCK) fp32[i] = 0u;
       // (the next tile's barrier orders these writes before its events)
@@ -1629,7 +1673,7 @@ int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int par
     // and its fingerprints) fill an SM with 48 warps, enough to hide the
     // dependent hash and probe latencies
     constexpr int BA = 512;
-    constexpr size_t smem = (size_t)kTileSlots * sizeof(Slot) + kFpBytes;
+    const size_t smem = (fresh ? kSoaTileBytes : (size_t)kTileSlots * sizeof(Slot)) + kFpBytes;
     auto kern = fresh ? k_tile_apply<BA, true, N> : k_tile_apply<BA, false, N>;
     DBG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
