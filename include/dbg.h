@@ -467,7 +467,7 @@ typedef struct dbg_sketch_item {
   uint32_t *registers;
 } dbg_sketch_item;
 
-/* dbg_sketch_reads for many read sets at once: one launch per up to 128
+/* dbg_sketch_reads for many read sets at once: one launch per up to 256
  * items, whose CTAs take (item, read tile) work units from one index space.
  * Each item's registers equal those dbg_sketch_reads gives it.  Asynchronous
  * on `stream`.  Errors: INVALID_ARG (k, NULL pointers), CUDA. */

@@ -1615,7 +1615,15 @@ int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int par
   mark(1, s);
   // bucket sizing: positions per item, then buckets and the region table
   {
-    const int gx = std::max(1, (sms * 4 + n - 1) / n);
+    // four CTAs per SM over the items, and more when the largest read set
+    // would take over 32 reads a thread (items of very uneven size: the
+    // largest one sets the time; the others' extra CTAs return at once), at
+    // most 16384 CTAs in all
+    uint64_t max_reads = 0;
+    for (int i = 0; i < n; ++i) max_reads = std::max<uint64_t>(max_reads, items[i].n_reads);
+    const uint64_t want = std::min<uint64_t>((max_reads + 256 * 32 - 1) / (256 * 32),
+                                             (uint64_t)std::max(1, 16384 / n));
+    const int gx = (int)std::max<uint64_t>(want, (uint64_t)std::max(1, (sms * 4 + n - 1) / n));
     k_bin_totals<N><<<dim3(gx, n), 256, 0, s>>>(pk, mv.totals, fresh ? 1 : 0);
     DBG_CK(cudaGetLastError());
     k_bin_buckets<N><<<1, 1024, 0, s>>>(pk, mv.totals, shift, parts, mv.begin, mv.cursor, sc.cap,

@@ -23,6 +23,8 @@ constexpr unsigned long long kSketchSalt = 0x9E3779B97F4A7C15ull;
 constexpr int kSketchRegs = DBG_SKETCH_REGISTERS;
 constexpr int kSketchRun = 16;  // positions of one read per thread and round
 constexpr int kSketchCtas = 7;  // CTAs of 256 threads per SM (shared memory allows 7)
+// read sets per launch: 256 descriptors (26.6 KB) still fit the kernel parameters
+constexpr int kSketchItems = 2 * kBatchItems;
 
 // Registers in shared memory (one read set per launch).  A register only
 // grows, and after the first few thousand keys almost no key raises it: a key
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(BLOCK, kSketchCtas)
 // the descriptor's table pointer) when its tiles of the item end.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kSketchCtas)
-    k_sketch_batch(const __grid_constant__ ItemPack<kBatchItems> pk, int tile_reads,
+    k_sketch_batch(const __grid_constant__ ItemPack<kSketchItems> pk, int tile_reads,
                    uint64_t chunk) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *s_reg = reinterpret_cast<uint32_t *>(smem + tile_smem_bytes(tile_reads));
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(BLOCK, kSketchCtas)
     const int it = find_item(pk, t);
     const uint64_t end = it + 1 < pk.n_items ? pk.d[it + 1].tile_begin : pk.total_tiles;
     const uint64_t tb = min(t1, end);
-    for_each_vertex<BLOCK, kBatchItems, kSketchRun>(pk, tile_reads, smem, vis, t, tb, 1);
+    for_each_vertex<BLOCK, kSketchItems, kSketchRun>(pk, tile_reads, smem, vis, t, tb, 1);
     __syncthreads();
     uint32_t *g = reinterpret_cast<uint32_t *>(pk.d[it].table);
     for (int j = threadIdx.x; j < kSketchRegs; j += BLOCK)
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(BLOCK, kSketchCtas)
 }
 
 // Every item's registers and status word := 0.
-__global__ void k_zero_registers(const __grid_constant__ ItemPack<kBatchItems> pk) {
+__global__ void k_zero_registers(const __grid_constant__ ItemPack<kSketchItems> pk) {
   const int i = blockIdx.x;
   uint32_t *r = reinterpret_cast<uint32_t *>(pk.d[i].table);
   for (int j = threadIdx.x; j <= kSketchRegs; j += blockDim.x) r[j] = 0u;
@@ -178,9 +180,9 @@ extern "C" int dbg_sketch_batch(const dbg_sketch_item *items, int n_items, void 
     DBG_CK(cudaFuncSetAttribute(k_sketch_batch<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sketch_batch<B>, B, smem));
-  for (int first = 0; first < n_items; first += kBatchItems) {
-    const int cnt = std::min(kBatchItems, n_items - first);
-    ItemPack<kBatchItems> pk{};
+  for (int first = 0; first < n_items; first += kSketchItems) {
+    const int cnt = std::min(kSketchItems, n_items - first);
+    ItemPack<kSketchItems> pk{};
     pk.n_items = cnt;
     uint64_t tiles = 0;
     for (int i = 0; i < cnt; ++i) {
