@@ -211,11 +211,15 @@ int dbg_insert_reads(dbg_handle h, const uint8_t *packed, const uint64_t *offset
  * memory gives asynchronous copies; pageable memory works but copies are
  * staged by the driver).  The reads are copied to device staging buffers
  * owned by the handle: whole, when packed bytes plus offsets take at most
- * 4 GiB, and inserted with one call; otherwise in chunks of at most 2^22
- * reads / 256 MiB, each chunk's copy overlapping the previous chunk's insert.
- * The offsets are validated on the host first (INVALID_ARG if one decreases).
- * Returns after the last insert has been launched; the host buffers may be
- * reused once `stream` has passed the call.
+ * 4 GiB, and inserted with one call -- the offsets first, then the bases in
+ * up to 8 parts of at least 128 MiB, the binned insert's scatter starting on
+ * each part as it arrives; otherwise in chunks of at most 2^22 reads /
+ * 256 MiB, each chunk's copy overlapping the previous chunk's insert.  The
+ * offsets are validated on the host, while the whole input's copies run or
+ * before the first chunk's; no kernel is launched when one decreases
+ * (INVALID_ARG, after the call's copies have finished).  Returns after the
+ * last insert has been launched; the host buffers may be reused once
+ * `stream` has passed the call.
  * Errors: as dbg_insert_reads, plus OOM for the staging buffers. */
 int dbg_insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
                           uint64_t n_reads, void *stream);

@@ -439,8 +439,9 @@ constexpr size_t scatter_smem(int tile_reads, int parts) {
 template <int BLOCK, int N>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
     k_bin_scatter(const __grid_constant__ ItemPack<N> pk, int tile_reads, int shift, int parts,
-                  uint64_t slices, const uint32_t *hist, unsigned long long *cursor, uint64_t *out,
-                  uint64_t cap, unsigned long long *ctr, uint32_t *use_binned,
+                  uint64_t t0, uint64_t t1, uint64_t slices, const uint32_t *hist,
+                  unsigned long long *cursor, uint64_t *out, uint64_t cap,
+                  unsigned long long *ctr, uint32_t *use_binned,
                   const unsigned long long *bucket_end) {
   if (ld_volatile_u32(use_binned) == 0u) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
     vis.bucket_end = bucket_end;
     vis.use_binned = use_binned;
   }
-  const uint64_t T = pk.total_tiles;
+  const uint64_t T = t1 - t0;  // this launch's read tiles: [t0, t1)
   for (int q = threadIdx.x; q < parts; q += BLOCK) vis.hist[q] = 0;
   for (;;) {
     const uint64_t sl = grab(&ctr[1]);
@@ -479,8 +480,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
       }
     }
     __syncthreads();
-    for_each_vertex<BLOCK, N, kRun>(pk, tile_reads, smem, vis, sl * T / slices,
-                                    (sl + 1) * T / slices, 1);
+    for_each_vertex<BLOCK, N, kRun>(pk, tile_reads, smem, vis, t0 + sl * T / slices,
+                                    t0 + (sl + 1) * T / slices, 1);
   }
 }
 
@@ -1597,7 +1598,7 @@ template <int N>
 int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int parts,
                 uint64_t tiles, uint64_t walk_tiles, const ItemDesc *direct,
                 uint64_t direct_tiles, const dbg_tuning &tuning, int sms, cudaStream_t s,
-                bool fresh, const Marks &mark) {
+                bool fresh, const Marks &mark, const InputParts *input = nullptr) {
   const int scatter_reads = scatter_tile_reads(tuning);
   const MetaView mv = meta_view(sc);
   const int tpr = 1 << (shift - kTileLog2);
@@ -1645,12 +1646,29 @@ int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int par
                                 (int)smem));
     int per_sm = 0;
     DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<BS, N>, BS, smem));
-    const int grid = (int)std::max<uint64_t>(
-        1, std::min<uint64_t>(slices, (uint64_t)std::max(1, per_sm) * sms));
-    k_bin_scatter<BS, N><<<grid, BS, smem, s>>>(pk, scatter_reads, shift, parts, slices,
-                                                mv.hist, mv.cursor, sc.ev, sc.cap, mv.ctr, mv.flag,
-                                                mv.begin + 1);
-    DBG_CK(cudaGetLastError());
+    // one launch over every read tile, or (input arriving in parts) one per
+    // part, each after its part's copy: tiles [cut[c], cut[c + 1]) hold reads
+    // that have all arrived (a tile split by a cut goes to the later part)
+    const int n_parts = (N == 1 && input != nullptr && input->n > 1) ? input->n : 1;
+    for (int c = 0; c < n_parts; ++c) {
+      uint64_t a = 0, b = walk_tiles;
+      if (n_parts > 1) {
+        a = c == 0 ? 0 : std::min<uint64_t>(walk_tiles, input->read_cut[c] / (uint64_t)scatter_reads);
+        b = c + 1 == n_parts
+                ? walk_tiles
+                : std::min<uint64_t>(walk_tiles, input->read_cut[c + 1] / (uint64_t)scatter_reads);
+        DBG_CK(cudaStreamWaitEvent(s, input->ready[c], 0));
+        if (b <= a) continue;
+        if (c > 0) DBG_CK(cudaMemsetAsync(mv.ctr + 1, 0, sizeof(unsigned long long), s));
+      }
+      const uint64_t sl = std::min<uint64_t>(b - a, kBinSlices);
+      const int grid = (int)std::max<uint64_t>(
+          1, std::min<uint64_t>(sl, (uint64_t)std::max(1, per_sm) * sms));
+      k_bin_scatter<BS, N><<<grid, BS, smem, s>>>(pk, scatter_reads, shift, parts, a, b, sl,
+                                                  mv.hist, mv.cursor, sc.ev, sc.cap, mv.ctr,
+                                                  mv.flag, mv.begin + 1);
+      DBG_CK(cudaGetLastError());
+    }
   }
   const uint64_t unit = tile_unit(tpr);
   mark(4, s);
@@ -1713,8 +1731,14 @@ int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int par
 
 }  // namespace
 
+int wait_input(const InputParts *input, cudaStream_t s) {
+  if (input != nullptr)
+    for (int c = 0; c < input->n; ++c) DBG_CK(cudaStreamWaitEvent(s, input->ready[c], 0));
+  return DBG_OK;
+}
+
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
-                  cudaStream_t s, int call, bool fresh) {
+                  cudaStream_t s, int call, bool fresh, const InputParts *input) {
   constexpr int B = 256;
   const dbg_tuning t = resolve_tuning(tuning);
   // the tiled apply re-partitions each region by tile, so its first pass can
@@ -1750,7 +1774,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     ItemDesc direct = it;
     direct.tile_begin = 0;
     DBG_TRY(tiled_chain<1>(h->bin, &walk, 1, geo.shift, geo.parts, n_tiles, walk_tiles, &direct,
-                           tiles, tuning, sms, s, fresh, mark));
+                           tiles, tuning, sms, s, fresh, mark, input));
     if (!capturing) DBG_CK(cudaEventRecord(h->bin.done, s));
     return DBG_OK;
   }
@@ -1758,6 +1782,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
   // the streaming apply: an exact count pass and its scan, the scatter into
   // gap-free region ranges, then the apply (a rebuild empties the table
   // first: this apply reads it)
+  DBG_TRY(wait_input(input, s));
   if (fresh) DBG_TRY(launch_table_init(h->table, h->n_slots, s));
   const MetaView mv = meta_view(h->bin);
   const int tile_reads = std::min(t.tile_reads, B);
@@ -1795,9 +1820,9 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     int per_sm = 0;
     DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<BS, 1>, BS, smem));
     const int grid = (int)std::min<uint64_t>(slices, (uint64_t)std::max(1, per_sm) * sms);
-    k_bin_scatter<BS, 1><<<grid, BS, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, slices,
-                                                mv.hist, mv.cursor, h->bin.ev, h->bin.cap, mv.ctr,
-                                                mv.flag, nullptr);
+    k_bin_scatter<BS, 1><<<grid, BS, smem, s>>>(pk, tile_reads, geo.shift, geo.parts, 0,
+                                                walk_tiles, slices, mv.hist, mv.cursor, h->bin.ev,
+                                                h->bin.cap, mv.ctr, mv.flag, nullptr);
     DBG_CK(cudaGetLastError());
   }
   mark(5, s);

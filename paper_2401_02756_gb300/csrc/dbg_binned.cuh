@@ -41,14 +41,30 @@ uint64_t bin_events_wanted(dbg_handle h);
 // (0: bin_events_wanted) and the meta area.
 int ensure_bin_scratch(dbg_handle h, uint64_t events);
 
+// A read set whose packed bases arrive in parts (host input copied part by
+// part on another stream): part c holds reads [read_cut[c], read_cut[c + 1])
+// and is in device memory once ready[c] has completed.  The offsets of every
+// read must be there before the call's first kernel.
+struct InputParts {
+  int n = 0;
+  const uint64_t *read_cut = nullptr;  // n + 1 read indices, from 0 to the read count
+  const cudaEvent_t *ready = nullptr;  // n events
+};
+
+// Make `s` wait for every part of `input` (when it is not null).
+int wait_input(const InputParts *input, cudaStream_t s);
+
 // Insert one read set through count / scan / scatter / apply, falling back to
 // the direct kernel on the device when the events do not fit the buffer.
 // `call`: the kernel timer's ring slot for this call (-1: not timed).
 // `fresh`: the table is rebuilt from empty (its contents are discarded); the
 // tiled apply then writes every tile from an EMPTY tile in shared memory
 // instead of reading it, which empties the table without a pass of its own.
+// `input`: the reads arrive in parts; the tiled chain's scatter takes each
+// part as it arrives, every other path waits for all of them first.
 int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tuning &tuning,
-                  cudaStream_t s, int call, bool fresh = false);
+                  cudaStream_t s, int call, bool fresh = false,
+                  const InputParts *input = nullptr);
 
 // Insert many read sets, each into its own table (k <= 31), through binned
 // chains: every chain is one launch of each binned kernel over all of its

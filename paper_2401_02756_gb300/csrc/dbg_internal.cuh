@@ -225,6 +225,7 @@ struct dbg_graph {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+  cudaEvent_t ev_part[8] = {};                // parts of a whole-input copy (kInputParts)
   // binned insert scratch (allocated when a single-read-set binned insert
   // first needs it; batched inserts use the library's own)
   dbg::BinScratch bin;

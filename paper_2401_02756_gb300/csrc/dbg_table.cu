@@ -230,6 +230,7 @@ int ensure_copy_stream(dbg_handle h) {
     DBG_CK(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
     DBG_CK(cudaEventCreateWithFlags(&h->ev_consumed[i], cudaEventDisableTiming));
   }
+  for (cudaEvent_t &e : h->ev_part) DBG_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   return DBG_OK;
 }
 
@@ -351,6 +352,8 @@ extern "C" void dbg_destroy(dbg_handle h) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
     if (h->ev_consumed[i]) cudaEventDestroy(h->ev_consumed[i]);
   }
+  for (cudaEvent_t e : h->ev_part)
+    if (e) cudaEventDestroy(e);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   dbg::free_bin_scratch(h->bin);
   cudaFree(h->d_spill);
@@ -534,13 +537,16 @@ bool want_binned(dbg_handle h) {
 // fresh: the table's contents are discarded first (dbg_build_reads); the
 // binned path folds that into its tiled apply, the others empty the table
 // with the init kernel before they insert.
+// `input`: the read set's bases arrive in parts (see dbg::InputParts); only
+// the binned scatter takes them part by part, every other kernel waits for all.
 int insert_one(dbg_handle h, const dbg::ItemDesc &it, uint64_t tiles, cudaStream_t s,
-               bool fresh = false) {
+               bool fresh = false, const dbg::InputParts *input = nullptr) {
   const int call = dbg::timer_begin_call(h);
   const bool binned = h->k <= 32 && want_binned(h) &&
                       (h->bin.cap == dbg::bin_events_wanted(h) ||
                        dbg::ensure_bin_scratch(h, 0) == DBG_OK);
-  if (binned) return dbg::launch_binned(h, it, tiles, h->tuning, s, call, fresh);
+  if (binned) return dbg::launch_binned(h, it, tiles, h->tuning, s, call, fresh, input);
+  DBG_TRY(dbg::wait_input(input, s));
   if (fresh) DBG_TRY(dbg::launch_table_init(h->table, h->n_slots, s));
   if (h->k > 32) {  // 128-bit keys: their own kernel
     dbg::timer_mark(h, call, 0, s);
@@ -605,6 +611,8 @@ namespace {
 constexpr uint64_t kStageAllBytes = 4ull << 30;  // inputs up to this size are staged whole
 constexpr uint64_t kStageBytes = 256ull << 20;   // otherwise: packed bytes per host chunk
 constexpr uint64_t kStageReads = 1ull << 22;     // otherwise: reads per host chunk
+constexpr int kInputParts = 8;                    // a whole input is copied in at most 8 parts
+constexpr uint64_t kPartBytes = 128ull << 20;     // of at least this many packed bytes
 
 int grow_stage(dbg_handle h, uint64_t bytes, uint64_t reads) {
   const int st = ensure_copy_stream(h);
@@ -664,34 +672,98 @@ static bool offsets_non_decreasing(const uint64_t *offsets, uint64_t n_reads) {
   return std::all_of(ok.begin(), ok.end(), [](char c) { return c != 0; });
 }
 
+// The whole input staged at once (one insert: the binned path needs to see
+// the whole read set).  The offsets are copied first, then the packed bases
+// in parts of at least kPartBytes, each recorded by an event, so that the
+// binned scatter starts on a part as soon as it has arrived.  The host checks
+// the offsets while the copies run; no kernel is launched before the check
+// passes (a refused call waits for its copies, so that the caller may reuse
+// its buffers).
+static int insert_whole(dbg_handle h, const uint8_t *packed, const uint64_t *offsets, uint64_t n_reads,
+                        uint64_t all_bytes, const dbg_tuning &t, cudaStream_t s, bool fresh) {
+  DBG_TRY(grow_stage(h, std::max<uint64_t>(16, (all_bytes + 15) & ~15ull), n_reads));
+  const uint64_t byte0 = offsets[0] >> 2, end = (offsets[n_reads] + 3) >> 2;
+  DBG_CK(cudaStreamWaitEvent(h->copy_stream, h->ev_consumed[0], 0));
+  DBG_CK(cudaMemcpyAsync(h->stage_offsets[0], offsets, (n_reads + 1) * sizeof(uint64_t),
+                         cudaMemcpyHostToDevice, h->copy_stream));
+  DBG_CK(cudaEventRecord(h->ev_copied[0], h->copy_stream));
+  // parts: the reads cut where the bytes pass equal shares
+  const int n_parts =
+      (int)std::min<uint64_t>(kInputParts, std::max<uint64_t>(1, all_bytes / kPartBytes));
+  uint64_t read_cut[kInputParts + 1];
+  read_cut[0] = 0;
+  read_cut[n_parts] = n_reads;
+  for (int c = 1; c < n_parts; ++c) {
+    const uint64_t target = byte0 + all_bytes * (uint64_t)c / (uint64_t)n_parts;
+    uint64_t lo = read_cut[c - 1], hi = n_reads;  // the first read starting at or past it
+    while (lo < hi) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      if ((offsets[mid] >> 2) < target)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    read_cut[c] = lo;
+  }
+  uint64_t copied = byte0;  // bytes [byte0, copied) are on their way
+  for (int c = 0; c < n_parts; ++c) {
+    const uint64_t upto =
+        c + 1 == n_parts
+            ? end
+            : std::max(copied, std::min(end, (offsets[read_cut[c + 1]] + 3) >> 2));
+    if (upto > copied)
+      DBG_CK(cudaMemcpyAsync(h->stage_packed[0] + (copied - byte0), packed + copied, upto - copied,
+                             cudaMemcpyHostToDevice, h->copy_stream));
+    copied = upto;
+    DBG_CK(cudaEventRecord(h->ev_part[c], h->copy_stream));
+  }
+  if (!offsets_non_decreasing(offsets, n_reads)) {
+    DBG_CK(cudaStreamSynchronize(h->copy_stream));
+    return DBG_ERR_INVALID_ARG;
+  }
+  if (fresh) DBG_TRY(clear_status(h, s));
+  DBG_CK(cudaStreamWaitEvent(s, h->ev_copied[0], 0));
+  const dbg::ItemDesc it =
+      dbg::make_item(h, h->stage_packed[0], h->stage_offsets[0], n_reads, byte0 * 4);
+  const uint64_t tiles = (n_reads + (uint64_t)t.tile_reads - 1) / (uint64_t)t.tile_reads;
+  dbg::InputParts input;
+  input.n = n_parts;
+  input.read_cut = read_cut;
+  input.ready = h->ev_part;
+  if (n_parts == 1) DBG_CK(cudaStreamWaitEvent(s, h->ev_part[0], 0));
+  DBG_TRY(insert_one(h, it, tiles, s, fresh, n_parts > 1 ? &input : nullptr));
+  DBG_CK(cudaEventRecord(h->ev_consumed[0], s));
+  return DBG_OK;
+}
+
 // dbg_insert_reads_host, or with `fresh` dbg_build_reads_host: the first
 // chunk's insert then discards the table's contents (later chunks add to it).
 static int insert_reads_host(dbg_handle h, const uint8_t *packed, const uint64_t *offsets,
                              uint64_t n_reads, void *stream, bool fresh) {
   if (!h) return DBG_ERR_INVALID_ARG;
   if (n_reads > 0 && (!packed || !offsets)) return DBG_ERR_INVALID_ARG;
-  if (n_reads > 0 && !offsets_non_decreasing(offsets, n_reads)) return DBG_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (fresh) {
+  if (n_reads == 0) {
+    if (!fresh) return DBG_OK;
     DBG_TRY(clear_status(h, s));
-    if (n_reads == 0) return dbg::launch_table_init(h->table, h->n_slots, s);
+    return dbg::launch_table_init(h->table, h->n_slots, s);
   }
-  if (n_reads == 0) return DBG_OK;
   const dbg_tuning t = dbg::resolve_tuning(h->tuning);
 
-  // chunk boundaries: the whole input when it is small enough (one insert,
-  // which the binned path needs to see the whole read set at once), else at
-  // most kStageReads reads and about kStageBytes bytes per chunk
+  // the whole input when it is small enough (one insert, which the binned
+  // path needs to see the whole read set at once), else chunks of at most
+  // kStageReads reads and about kStageBytes bytes
+  if (offsets[n_reads] >= offsets[0]) {
+    const uint64_t all_bytes = ((offsets[n_reads] + 3) >> 2) - (offsets[0] >> 2);
+    if (all_bytes + (n_reads + 1) * sizeof(uint64_t) <= kStageAllBytes)
+      return insert_whole(h, packed, offsets, n_reads, all_bytes, t, s, fresh);
+  }
+  if (!offsets_non_decreasing(offsets, n_reads)) return DBG_ERR_INVALID_ARG;
+  if (fresh) DBG_TRY(clear_status(h, s));
   std::vector<uint64_t> cuts{0};
   uint64_t max_bytes = 0, max_reads = 0;
-  const uint64_t all_bytes = ((offsets[n_reads] + 3) >> 2) - (offsets[0] >> 2);
-  if (all_bytes + (n_reads + 1) * sizeof(uint64_t) <= kStageAllBytes) {
-    cuts.push_back(n_reads);
-    max_bytes = all_bytes;
-    max_reads = n_reads;
-  }
   for (uint64_t r0 = 0; cuts.back() != n_reads && r0 < n_reads;) {
     const uint64_t b0 = offsets[r0] >> 2;
     uint64_t r1 = std::min(n_reads, r0 + kStageReads);

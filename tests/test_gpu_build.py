@@ -129,6 +129,15 @@ def test_build_host_and_empty_build(path):
     g.build_host(rs.packed, rs.offsets)
     assert g.status() == dbg.OK
     assert_same_graph(g.export(), oracle_export(rs))
+    # offsets that decrease are refused (checked while the input is copied)
+    # before any kernel runs: the graph stays as it was
+    bad = rs.offsets.copy()
+    bad[1000] = bad[999] - 1
+    with pytest.raises(dbg.DbgError) as e:
+        g.build_host(rs.packed, bad)
+    assert e.value.code == dbg.ERR_INVALID_ARG
+    assert g.status() == dbg.OK
+    assert_same_graph(g.export(), oracle_export(rs))
     empty = np.zeros(1, dtype=np.uint64)
     g.build_host(np.zeros(1, np.uint8), empty)  # no reads: the table is only emptied
     assert g.stats() == (0, 0)

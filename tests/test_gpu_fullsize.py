@@ -42,8 +42,13 @@ def test_full_size_workload_matches_oracle_digests(name):
     g = dbg.Graph(rs.k, int(math.ceil(1.5 * gold["n_vertices"])))
     packed, offsets = to_device(rs)
     # an insert into the fresh table, then the benchmark's step -- a build
-    # (dbg_build_reads) into the table that already holds the graph
-    for step in (g.insert, g.build):
+    # (dbg_build_reads) into the table that already holds the graph -- then
+    # the same build from host memory (the 100 Mbp input is copied in parts,
+    # the binned scatter starting on each part as it arrives)
+    def build_host(_packed, _offsets):
+        g.build_host(rs.packed, rs.offsets)
+
+    for step in (g.insert, g.build, build_host):
         step(packed, offsets)
         assert g.status() == dbg.OK
         if g.info()["table_bytes"] >= 256 << 20:  # binned path: it did the work, no fall-back
