@@ -325,7 +325,11 @@ int dbg_grow(dbg_handle h, uint64_t new_capacity, void *stream);
 int dbg_get_status(dbg_handle h, void *stream);
 
 /* Wait for `stream`, then count the vertices and the edges (the sum of all
- * counters) of the graph.  Either output pointer may be NULL.
+ * counters) of the graph.  Either output pointer may be NULL.  When the last
+ * call that changed the graph was a dbg_build_reads(_host) on the tiled
+ * binned path, the build counted its new vertices and its k-mers as it went
+ * and those counts are returned, without a pass over the table (unless the
+ * build gave its work to the direct insert).
  * Returns the sticky status when it is not DBG_OK (outputs still written). */
 int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, void *stream);
 

@@ -193,13 +193,14 @@ __global__ void __launch_bounds__(1024)
 // keys) clears the use-binned flag, and the direct insert does the call
 // instead, exactly as when the events exceed the buffer.
 
-// totals[i] = vertex positions of item i's reads, sum of max(0, len - k + 2)
-// (grid: x strides over the item's reads, y = item).
+// totals[i] = vertex positions of item i's reads, sum of max(0, len - k + 2),
+// and edges[i] = its k-mers, sum of max(0, len - k + 1) (grid: x strides over
+// the item's reads, y = item).
 // clear: also zero every item's sticky status and spill count (a rebuild
 // from empty; this is the chain's first kernel, so every later one sees it).
 template <int N>
 __global__ void k_bin_totals(const __grid_constant__ ItemPack<N> pk, unsigned long long *totals,
-                             int clear) {
+                             unsigned long long *edges, int clear) {
   const int i = blockIdx.y;
   if (i >= pk.n_items) return;
   if (clear && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -209,15 +210,24 @@ __global__ void k_bin_totals(const __grid_constant__ ItemPack<N> pk, unsigned lo
   const uint64_t *offsets = pk.d[i].offsets;
   const uint64_t n_reads = pk.d[i].n_reads;
   const int k = pk.d[i].k;
-  unsigned long long v = 0;
+  unsigned long long v = 0, ne = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += stride) {
     const uint64_t a = offsets[r], b = offsets[r + 1];
     const uint64_t len = b > a ? b - a : 0;
-    v += len >= (uint64_t)k ? len - k + 2 : 0;
+    if (len >= (uint64_t)k) {
+      v += len - k + 2;
+      ne += len - k + 1;
+    }
   }
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(&totals[i], v);
+  for (int d = 16; d > 0; d >>= 1) {
+    v += __shfl_down_sync(kFull, v, d);
+    ne += __shfl_down_sync(kFull, ne, d);
+  }
+  if ((threadIdx.x & 31) == 0 && v) {
+    atomicAdd(&totals[i], v);
+    atomicAdd(&edges[i], ne);
+  }
 }
 
 // Exclusive prefix over a CTA of 1024 threads; `total` receives the sum.
@@ -257,10 +267,19 @@ __device__ __forceinline__ unsigned long long cta1024_exclusive_scan(unsigned lo
 template <int N>
 __global__ void __launch_bounds__(1024)
     k_bin_buckets(const __grid_constant__ ItemPack<N> pk, const unsigned long long *totals,
-                  int shift, int parts, unsigned long long *begin, unsigned long long *cursor,
-                  uint64_t cap, unsigned long long *ctr, uint32_t *use_binned, TileAux aux) {
+                  const unsigned long long *edges, int fresh, int shift, int parts,
+                  unsigned long long *begin, unsigned long long *cursor, uint64_t cap,
+                  unsigned long long *ctr, uint32_t *use_binned, TileAux aux) {
   __shared__ unsigned long long s_warp[32];
   const int tid = threadIdx.x;
+  if (tid < pk.n_items) {  // a rebuild counts its vertices (its claims) and its edges
+    uint32_t *st = pk.d[tid].status;
+    *small_counted(st) = fresh ? 1u : 0u;
+    if (fresh) {
+      small_built(st)[0] = 0ull;
+      small_built(st)[1] = edges[tid];
+    }
+  }
   unsigned long long bk[2], nt[2];
   for (int j = 0; j < 2; ++j) {
     const int p = 2 * tid + j;
@@ -1138,6 +1157,18 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 thr
   uint32_t *fp32 = reinterpret_cast<uint32_t *>(fp);
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_stop, s_failed;
+  // a rebuild counts its vertices: every slot of a fresh tile that holds a key
+  // (a non-zero fingerprint) was claimed in that tile (the deferred pass
+  // counts the rest); the count goes to the item's built counts whenever the
+  // item changes, and at the end
+  uint32_t *cur_status = N == 1 ? pk.d[0].status : nullptr;
+  uint32_t claimed = 0;
+  auto flush_claims = [&]() {
+    const uint32_t w = __reduce_add_sync(kFull, claimed);
+    if ((threadIdx.x & 31) == 0 && w && cur_status != nullptr)
+      atomicAdd(small_built(cur_status), (unsigned long long)w);
+    claimed = 0;
+  };
   if constexpr (FRESH) {
     empty_soa_tile(soa, fp32);
   } else if (threadIdx.x == 0) {
@@ -1166,6 +1197,10 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 thr
     const int len = (int)min((uint64_t)kTileSlots, n_slots - first);
     uint64_t e[kBatch];
     if constexpr (FRESH) {
+      if (N > 1 && status != cur_status) {  // (the same for the whole CTA)
+        flush_claims();
+        cur_status = status;
+      }
       uint4 *dst = reinterpret_cast<uint4 *>(table + first);
       if (a == b) {  // no event: the tile is written as it starts, EMPTY
         const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
@@ -1260,7 +1295,11 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 thr
         }
         __stcs(dst + i, v);
       }
-      for (int i = threadIdx.x; i < kFpBytes / 4; i += BLOCK) fp32[i] = 0u;
+      for (int i = threadIdx.x; i < kFpBytes / 4; i += BLOCK) {
+        const uint32_t w = fp32[i];  // four fingerprints: non-zero for a key
+        claimed += (uint32_t)__popc((((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u);
+        fp32[i] = 0u;
+      }
       // (the next tile's barrier orders these writes before its events)
     } else if (threadIdx.x == 0 && s_stop == 0u) {
       fence_proxy_async_smem();  // the CTA's shared-memory updates, before the bulk read
@@ -1268,24 +1307,31 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)  // three CTAs of 512 thr
       bulk_commit();
     }
   }
+  if constexpr (FRESH) flush_claims();
   if (!FRESH && threadIdx.x == 0) bulk_wait_all();
 }
 
 // One event, from its home slot, with the global find-or-claim (its tile is
 // final by now).
-__device__ __forceinline__ void global_event(uint64_t e, const ItemDesc &it) {
+// Returns 1 when the event claimed a new slot (a new vertex), else 0.
+__device__ __forceinline__ uint32_t global_event(uint64_t e, const ItemDesc &it) {
   const unsigned long long key = e >> 3;
   uint64_t s;
-  if (find_or_claim(it.table, it.n_slots, it.max_probes, key, s)) {
+  bool claimed = false;
+  if (find_or_claim(it.table, it.n_slots, it.max_probes, key, s, &claimed)) {
     if (e & 4ull) atomicAdd(&it.table[s].cnt[e & 3ull], 1u);
   } else {
     spill_or_fail(it.spill, it.spill_cap, it.spill_count, it.status, key, (e & 4ull) != 0,
                   (uint32_t)(e & 3ull));
   }
+  return claimed ? 1u : 0u;
 }
 
 // The events that left their tile (each region's list), then those of the
-// overflow area ((event, region) pairs), from their home slots.
+// overflow area ((event, region) pairs), from their home slots.  New
+// vertices are added to their graph's built counts (meaningful only on a
+// rebuild, which zeroed them): one atomic per warp and region, and for the
+// overflow area one per warp of a single table, else one per new vertex.
 template <int N>
 __global__ void k_tile_deferred(const __grid_constant__ ItemPack<N> pk,
                                 const uint64_t *__restrict__ ev,
@@ -1298,13 +1344,29 @@ __global__ void k_tile_deferred(const __grid_constant__ ItemPack<N> pk,
     if (threadIdx.x == 0) atomicAdd(aux.deferred, (unsigned long long)n);
     const ItemDesc &it = pk.d[aux.region_item[p]];
     const uint64_t *list = ev + begin[p];
-    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) global_event(list[i], it);
+    uint32_t claimed = 0;
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) claimed += global_event(list[i], it);
+    claimed = __reduce_add_sync(kFull, claimed);
+    if ((threadIdx.x & 31) == 0 && claimed)
+      atomicAdd(small_built(it.status), (unsigned long long)claimed);
   }
   const uint64_t no = *aux.overflow;  // (all of it written: the flag is still set)
   const uint64_t *over = ev2 + aux.region_base[parts];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < no; i += stride)
-    global_event(over[2 * i], pk.d[aux.region_item[over[2 * i + 1]]]);
+  uint32_t claimed = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < no; i += stride) {
+    const ItemDesc &it = pk.d[aux.region_item[over[2 * i + 1]]];
+    const uint32_t c = global_event(over[2 * i], it);
+    if (N == 1)
+      claimed += c;
+    else if (c)
+      atomicAdd(small_built(it.status), 1ull);
+  }
+  if (N == 1) {
+    claimed = __reduce_add_sync(kFull, claimed);
+    if ((threadIdx.x & 31) == 0 && claimed)
+      atomicAdd(small_built(pk.d[0].status), (unsigned long long)claimed);
+  }
 }
 
 // Empty every item's table (grid: x strides over the slots, y = item); with
@@ -1320,6 +1382,9 @@ __global__ void k_tables_init(const __grid_constant__ ItemPack<N> pk, const uint
     *pk.d[i].status = 0u;
     *pk.d[i].spill_count = 0ull;
   }
+  // (the gated form runs when a binned chain gave its call to the direct
+  // insert, which counts nothing)
+  if (gate != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *small_counted(pk.d[i].status) = 0u;
   uint4 *t = reinterpret_cast<uint4 *>(pk.d[i].table);
   const uint64_t n_vec = 2 * pk.d[i].n_slots;
   const uint4 head = make_uint4(0xffffffffu, 0xffffffffu, 0u, 0u);
@@ -1354,6 +1419,7 @@ struct MetaView {
   uint32_t *flag;
   unsigned long long *apply_ctr;  // kBinApplyCounters
   unsigned long long *totals;  // kBatchItems: vertex positions per item
+  unsigned long long *edges;   // kBatchItems: edges (k-mers) per item
   uint32_t *hist;              // kBinSlices * kBinMaxParts
 };
 
@@ -1367,7 +1433,8 @@ MetaView meta_view(const BinScratch &sc) {
   v.flag = reinterpret_cast<uint32_t *>(v.ctr + 3);
   v.apply_ctr = v.ctr + 4;
   v.totals = v.apply_ctr + (size_t)kBinMaxParts * kBinApplyCounters;
-  v.hist = reinterpret_cast<uint32_t *>(v.totals + kBatchItems);
+  v.edges = v.totals + kBatchItems;
+  v.hist = reinterpret_cast<uint32_t *>(v.edges + kBatchItems);
   return v;
 }
 
@@ -1611,6 +1678,7 @@ int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int par
   DBG_CK(cudaMemsetAsync(mv.ctr, 0, 4 * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.counts, 0, parts * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(mv.totals, 0, n * sizeof(unsigned long long), s));
+  DBG_CK(cudaMemsetAsync(mv.edges, 0, n * sizeof(unsigned long long), s));
   DBG_CK(cudaMemsetAsync(aux.fill, 0, tiles * sizeof(uint32_t), s));
   sc.counters = aux.overflow;
   mark(1, s);
@@ -1625,10 +1693,10 @@ int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int par
     const uint64_t want = std::min<uint64_t>((max_reads + 256 * 32 - 1) / (256 * 32),
                                              (uint64_t)std::max(1, 16384 / n));
     const int gx = (int)std::max<uint64_t>(want, (uint64_t)std::max(1, (sms * 4 + n - 1) / n));
-    k_bin_totals<N><<<dim3(gx, n), 256, 0, s>>>(pk, mv.totals, fresh ? 1 : 0);
+    k_bin_totals<N><<<dim3(gx, n), 256, 0, s>>>(pk, mv.totals, mv.edges, fresh ? 1 : 0);
     DBG_CK(cudaGetLastError());
-    k_bin_buckets<N><<<1, 1024, 0, s>>>(pk, mv.totals, shift, parts, mv.begin, mv.cursor, sc.cap,
-                                        mv.ctr, mv.flag, aux);
+    k_bin_buckets<N><<<1, 1024, 0, s>>>(pk, mv.totals, mv.edges, fresh ? 1 : 0, shift, parts,
+                                        mv.begin, mv.cursor, sc.cap, mv.ctr, mv.flag, aux);
     DBG_CK(cudaGetLastError());
     if (N > 1) {
       k_tile_map<<<parts, 256, 0, s>>>(aux, parts, mv.flag);
@@ -1775,6 +1843,7 @@ int launch_binned(dbg_handle h, const ItemDesc &it, uint64_t tiles, const dbg_tu
     direct.tile_begin = 0;
     DBG_TRY(tiled_chain<1>(h->bin, &walk, 1, geo.shift, geo.parts, n_tiles, walk_tiles, &direct,
                            tiles, tuning, sms, s, fresh, mark, input));
+    h->built_counts = fresh;  // a rebuild counted its vertices and edges (unless it fell back)
     if (!capturing) DBG_CK(cudaEventRecord(h->bin.done, s));
     return DBG_OK;
   }

@@ -18,10 +18,11 @@ constexpr int kBinApplyCounters = 64;                // apply: chunk counters pe
 
 // meta area: begin[kBinMaxParts + 1] | counts[kBinMaxParts] | cursor[kBinMaxParts] |
 // counters[4] (the last holds the flag) | apply counters[kBinMaxParts][kBinApplyCounters] |
-// item totals[kBatchItems] | slice histograms u32[kBinSlices][kBinMaxParts]
+// item totals[kBatchItems] | item edges[kBatchItems] | slice histograms
+// u32[kBinSlices][kBinMaxParts]
 constexpr size_t kBinMetaBytes =
     ((size_t)kBinMaxParts + 1) * 8 + 2 * (size_t)kBinMaxParts * 8 + 4 * 8 +
-    (size_t)kBinMaxParts * kBinApplyCounters * 8 + (size_t)kBatchItems * 8 +
+    (size_t)kBinMaxParts * kBinApplyCounters * 8 + 2 * (size_t)kBatchItems * 8 +
     (size_t)kBinSlices * kBinMaxParts * 4;
 
 struct BinGeometry {

@@ -264,6 +264,7 @@ int read_status(dbg_handle h, cudaStream_t s) {
 extern "C" int dbg_normalize(dbg_handle h, double divisor, void *stream) {
   using namespace dbg;
   if (!h || !(divisor > 0.0) || !isfinite(divisor)) return DBG_ERR_INVALID_ARG;
+  h->built_counts = false;  // the counters change
   Guard g(h->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -280,6 +281,7 @@ extern "C" int dbg_find_contigs(dbg_handle h, char *bases_out, uint64_t max_base
                                 uint64_t *n_bases, void *stream) {
   using namespace dbg;
   if (!h || !n_contigs || !n_bases || h->k > 32) return DBG_ERR_INVALID_ARG;
+  h->built_counts = false;  // (this pass takes the stats accumulators as scratch)
   Guard g(h->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -159,8 +159,10 @@ __device__ __forceinline__ uint64_t key_from_words(uint64_t lo, uint64_t hi, uin
 // (Alg. 4's search and Alg. 3's insertion, as open addressing: linear
 // probing from the home slot, a relaxed load first, atomicCAS only on EMPTY).
 // Returns false after max_probes slots without success.
+// `claimed` (optional): set when this call claimed the slot (a new vertex).
 __device__ __forceinline__ bool find_or_claim(Slot *table, uint64_t n_slots, uint32_t max_probes,
-                                              uint64_t key, uint64_t &slot_out) {
+                                              uint64_t key, uint64_t &slot_out,
+                                              bool *claimed = nullptr) {
   uint64_t s = home_slot(key, n_slots);
   for (uint32_t i = 0; i < max_probes; ++i) {
     unsigned long long cur = ld_relaxed_u64(&table[s].key);
@@ -172,6 +174,7 @@ __device__ __forceinline__ bool find_or_claim(Slot *table, uint64_t n_slots, uin
       unsigned long long prev = atomicCAS(&table[s].key, kEmpty, (unsigned long long)key);
       if (prev == kEmpty || prev == key) {
         slot_out = s;
+        if (claimed) *claimed = prev == kEmpty;
         return true;
       }
     }
@@ -180,6 +183,20 @@ __device__ __forceinline__ bool find_or_claim(Slot *table, uint64_t n_slots, uin
   return false;
 }
 
+
+// Every graph's small block of device memory (64 bytes beside its table):
+// the sticky status (u32) at byte 0; a flag at 4 set by a rebuild from empty
+// on the tiled binned path whose vertex and edge counts at 40 and 48 are then
+// exact (cleared when the build falls back to the direct insert); the stats
+// accumulators (2 x u64) at 16; the spill count (u64) at 32.  Kernels reach
+// the flag and the counts from an item's status pointer.
+constexpr size_t kSmallCounted = 4, kSmallAcc = 16, kSmallSpill = 32, kSmallBuilt = 40;
+__host__ __device__ inline uint32_t *small_counted(uint32_t *status) {
+  return reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(status) + kSmallCounted);
+}
+__host__ __device__ inline unsigned long long *small_built(uint32_t *status) {
+  return reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(status) + kSmallBuilt);
+}
 
 // Scratch of the binned insert: event buffers and bookkeeping, owned by a
 // handle (its single-read-set inserts) or by the library (batched inserts).
@@ -230,6 +247,10 @@ struct dbg_graph {
   // first needs it; batched inserts use the library's own)
   dbg::BinScratch bin;
   uint64_t bin_want = 0;                    // events asked for by dbg_reserve_events (0: default)
+  // the last call that changed the graph was a rebuild on the tiled binned
+  // path, which counts its vertices and edges (see small_counted): dbg_stats
+  // then reads them instead of counting the table
+  bool built_counts = false;
   // optional per-kernel timing of insert calls (dbg_enable_kernel_timing)
   int timer_cap = 0;                        // calls kept
   int timer_calls = 0;                      // calls recorded (may exceed timer_cap)

@@ -261,11 +261,12 @@ int device_of(dbg_handle h) {
 
 void carve_small(dbg_handle h, void *small) {
   h->d_status = static_cast<uint32_t *>(small);
-  h->d_acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 16);
-  h->d_spill_count = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + 32);
+  h->d_acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + dbg::kSmallAcc);
+  h->d_spill_count =
+      reinterpret_cast<unsigned long long *>(static_cast<char *>(small) + dbg::kSmallSpill);
 }
 
-constexpr uint64_t kSmallBytes = 64;   // status, stats accumulators, spill count
+constexpr uint64_t kSmallBytes = 64;   // the small block: status, flag, counters (dbg::kSmall*)
 constexpr uint64_t kOnMemTail = 256;   // the same block at the end of caller memory
 
 }  // namespace
@@ -363,6 +364,7 @@ extern "C" void dbg_destroy(dbg_handle h) {
 
 extern "C" int dbg_reset(dbg_handle h, void *stream) {
   if (!h) return DBG_ERR_INVALID_ARG;
+  h->built_counts = false;
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -420,6 +422,7 @@ extern "C" int dbg_get_info(dbg_handle h, dbg_info *out) {
 
 extern "C" int dbg_set_spill(dbg_handle h, uint64_t records) {
   if (!h || (h->k > 32 && records > 0)) return DBG_ERR_INVALID_ARG;  // 64-bit spill records
+  h->built_counts = false;
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   DBG_CK(cudaDeviceSynchronize());
@@ -440,6 +443,7 @@ extern "C" int dbg_set_spill(dbg_handle h, uint64_t records) {
 
 extern "C" int dbg_grow(dbg_handle h, uint64_t new_capacity, void *stream) {
   if (!h || h->k > 32) return DBG_ERR_INVALID_ARG;
+  h->built_counts = false;
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   return dbg::launch_grow(h, new_capacity, static_cast<cudaStream_t>(stream));
@@ -541,6 +545,7 @@ bool want_binned(dbg_handle h) {
 // the binned scatter takes them part by part, every other kernel waits for all.
 int insert_one(dbg_handle h, const dbg::ItemDesc &it, uint64_t tiles, cudaStream_t s,
                bool fresh = false, const dbg::InputParts *input = nullptr) {
+  h->built_counts = false;  // (set again by a rebuild on the tiled binned path)
   const int call = dbg::timer_begin_call(h);
   const bool binned = h->k <= 32 && want_binned(h) &&
                       (h->bin.cap == dbg::bin_events_wanted(h) ||
@@ -583,7 +588,9 @@ namespace {
 
 // The sticky status and the spill count back to zero, stream-ordered (the
 // part of dbg_reset that is not the table).
+// (the start of every rebuild: its counts, if any, are set by its insert)
 int clear_status(dbg_handle h, cudaStream_t s) {
+  h->built_counts = false;
   DBG_CK(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s));
   DBG_CK(cudaMemsetAsync(h->d_spill_count, 0, sizeof(unsigned long long), s));
   return DBG_OK;
@@ -834,6 +841,7 @@ static int insert_batch(const dbg_batch_item *items, int n_items, void *stream, 
     if (!items[i].graph || items[i].graph->device != dev) return DBG_ERR_INVALID_ARG;
     if (items[i].n_reads > 0 && (!items[i].packed || !items[i].offsets)) return DBG_ERR_INVALID_ARG;
   }
+  for (int i = 0; i < n_items; ++i) items[i].graph->built_counts = false;  // (dbg_stats counts)
   DeviceGuard g(dev);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -922,6 +930,22 @@ extern "C" int dbg_stats(dbg_handle h, uint64_t *n_vertices, uint64_t *n_edges, 
   DeviceGuard g(h->device);
   if (g.err != cudaSuccess) return dbg::cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->built_counts) {
+    // the graph was last rebuilt on the tiled binned path, which counted its
+    // new vertices and its edges: read them unless the build fell back
+    uint32_t head[2] = {0, 0};  // status, counted flag
+    unsigned long long built[2] = {0, 0}, spilled = 0;
+    DBG_CK(cudaMemcpyAsync(head, h->d_status, sizeof(head), cudaMemcpyDeviceToHost, s));
+    DBG_CK(cudaMemcpyAsync(built, dbg::small_built(h->d_status), sizeof(built),
+                           cudaMemcpyDeviceToHost, s));
+    DBG_CK(cudaMemcpyAsync(&spilled, h->d_spill_count, sizeof(spilled), cudaMemcpyDeviceToHost, s));
+    DBG_CK(cudaStreamSynchronize(s));
+    if (head[1] == 1u && head[0] == DBG_OK && spilled == 0) {
+      if (n_vertices) *n_vertices = built[0];
+      if (n_edges) *n_edges = built[1];
+      return DBG_OK;
+    }
+  }
   int st = dbg::launch_stats(h->table, h->n_slots, h->d_acc, s, h->k > 32);
   if (st != DBG_OK) return st;
   unsigned long long acc[2] = {0, 0};

@@ -52,11 +52,18 @@ def test_build_discards_what_the_table_held(k, capacity, tuning):
         assert g.binned_counters()["binned"]
     exp = oracle_export(rs)
     assert_same_graph(g.export(), exp)
+    # the vertex and edge totals: counted by the tiled build itself, or by a
+    # pass over the table
+    assert g.stats() == (len(exp[0]), rs.n_edges())
     g.build(packed, offsets)  # again: the same graph, not twice the counts
     assert_same_graph(g.export(), exp)
+    assert g.stats() == (len(exp[0]), rs.n_edges())
     g.insert(packed, offsets)  # an insert after a build adds as usual
+    assert g.stats() == (len(exp[0]), 2 * rs.n_edges())
     keys, counts = g.export()
     assert np.array_equal(keys, exp[0]) and np.array_equal(counts, 2 * exp[1])
+    g.normalize(2.0)  # (the counters change: the totals are counted again)
+    assert g.stats() == (len(exp[0]), rs.n_edges())
     g.close()
 
 
@@ -87,6 +94,7 @@ def test_build_at_high_load_defers_exactly(fill):
     c = g.binned_counters()
     assert c["binned"] and c["deferred"] > 0, c
     assert_same_graph(g.export(), exp)
+    assert g.stats() == (len(exp[0]), rs.n_edges())  # deferred vertices counted too
     g.close()
 
 
@@ -104,7 +112,9 @@ def test_build_falls_back_to_the_direct_insert_on_an_emptied_table():
     assert not g.binned_counters()["binned"]
     t = g.kernel_times()
     assert t[-1, dbg.Graph.KERNELS.index("direct_fallback")] >= 0
-    assert_same_graph(g.export(), oracle_export(rs))
+    exp = oracle_export(rs)
+    assert_same_graph(g.export(), exp)
+    assert g.stats() == (len(exp[0]), rs.n_edges())  # the fall-back counts nothing itself
     g.close()
 
 
