@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kCompactBlock)
 // serialised on that counter.
 constexpr int kRunBlock = 256;
 constexpr int kRunCtas = 1216;  // 8 CTAs of 256 threads on each of 152 SMs
+constexpr int kRunGroups = 4;   // blocks of kRunBlock positions a thread takes per round
 
 struct RunLists {
   uint64_t chunk;    // positions per CTA
@@ -176,9 +177,12 @@ struct RunLists {
   uint64_t bytes() const { return (uint64_t)ctas * (mid_cap + lng_cap) * 8; }
 };
 
-RunLists run_lists(uint64_t D) {
+// The lists for D positions over at most `ctas` CTAs (the scratch is sized
+// for kRunCtas; a launch over fewer CTAs uses that layout only when its lists
+// fit in those bytes).
+RunLists run_lists(uint64_t D, int ctas = kRunCtas) {
   RunLists r;
-  const uint64_t per = (D + kRunCtas - 1) / kRunCtas;
+  const uint64_t per = (D + ctas - 1) / ctas;
   r.chunk = std::max<uint64_t>(kRunBlock, (per + kRunBlock - 1) / kRunBlock * kRunBlock);
   r.ctas = (int)std::max<uint64_t>(1, (D + r.chunk - 1) / r.chunk);
   r.mid_cap = r.chunk / (kShortRun + 1) + 1;  // runs that start in a chunk, at most
@@ -211,13 +215,28 @@ __global__ void __launch_bounds__(kRunBlock)
   unsigned long long *my_mid = mid + (uint64_t)blockIdx.x * mid_cap;
   unsigned long long *my_lng = lng + (uint64_t)blockIdx.x * lng_cap;
   // (the loop bound is the CTA's, so every lane takes part in the ballots)
-  for (uint64_t base = c0; base < c1; base += kRunBlock) {
+  // kRunGroups blocks of positions a round: their keys are loaded first, so
+  // that the loads' latencies overlap; a short run's sort may rewrite keys of
+  // a later block of the round, but only within one run, whose keys share the
+  // prefix the later block compares
+  for (uint64_t round = c0; round < c1; round += (uint64_t)kRunBlock * kRunGroups) {
+  unsigned long long gkey[kRunGroups];
+  uint64_t gprev[kRunGroups];
+#pragma unroll
+  for (int g = 0; g < kRunGroups; ++g) {
+    const uint64_t i = round + (uint64_t)g * kRunBlock + threadIdx.x;
+    gkey[g] = i < n ? keys[i] : 0ull;
+    gprev[g] = (lane == 0 && i < n && i > 0) ? keys[i - 1] : 0ull;
+  }
+#pragma unroll
+  for (int g = 0; g < kRunGroups; ++g) {
+    const uint64_t base = round + (uint64_t)g * kRunBlock;
     const uint64_t i = base + threadIdx.x;
     const bool in = i < n;
-    const unsigned long long key = in ? keys[i] : 0ull;
+    const unsigned long long key = gkey[g];
     const uint64_t p = key >> pshift;
     uint64_t pp = __shfl_up_sync(0xffffffffu, p, 1);
-    if (lane == 0) pp = (in && i > 0) ? (keys[i - 1] >> pshift) : ~p;
+    if (lane == 0) pp = (in && i > 0) ? (gprev[g] >> pshift) : ~p;
     const bool bnd = in && (i == 0 || pp != p);  // a run starts here
     const unsigned bmask = __ballot_sync(0xffffffffu, bnd);
     uint32_t L = 0;
@@ -287,6 +306,7 @@ __global__ void __launch_bounds__(kRunBlock)
         counts[i + a] = rc[a];
       }
     }
+  }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -632,9 +652,14 @@ int export_prefix(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts
   const bool in_place = in_place_outputs(keys_out, counts_out);
   if ((caller || compacted) && !in_place) return DBG_ERR_INVALID_ARG;
   if (stride == 0) stride = D;
-  PrefixScratch ps;
+  PrefixScratch ps{};
   DBG_TRY(prefix_scratch(h->k, D, in_place, ps));
-  const RunLists rl = run_lists(D);
+  // one wave of the run pass: as many CTAs as fit on the device at once
+  int run_per_sm = 0;
+  DBG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&run_per_sm, k_sort_runs, kRunBlock, 0));
+  RunLists rl =
+      run_lists(D, std::max(1, std::min(kRunCtas, std::max(1, run_per_sm) * std::max(1, h->sm_count))));
+  if (rl.bytes() > run_lists(D).bytes()) rl = run_lists(D);  // (chunk rounding: the sized layout)
   char *buf = nullptr;
   if (caller) {
     if (caller_bytes < ps.total || ((uintptr_t)caller & 255u)) return DBG_ERR_INVALID_ARG;
@@ -731,7 +756,7 @@ int export_prefix(dbg_handle h, uint64_t D, uint64_t *keys_out, uint32_t *counts
 
 // Scratch of an in-place prefix export (see export_prefix).
 int prefix_scratch_bytes(int k, uint64_t D, uint64_t &bytes) {
-  PrefixScratch ps;
+  PrefixScratch ps{};
   DBG_TRY(prefix_scratch(k, D, true, ps));
   bytes = ps.total;
   return DBG_OK;
