@@ -47,7 +47,7 @@ constexpr int kMaxParts = kBinMaxParts;
 constexpr int kRun = 8;             // consecutive vertex positions per thread (rolled keys)
 
 constexpr int kTileLog2 = 11;
-constexpr int kTileSlots = 1 << kTileLog2;  // 2048 slots = 64 KB of shared memory
+constexpr int kTileSlots = 1 << kTileLog2;  // 2048 slots: 64 KB as 32-byte slots, 48 KB split
 constexpr int kMaxTilesPerRegion = 4096;    // beyond this the streaming apply is used
 constexpr int kTiledShift = 21;             // automatic regions of the tiled path: 1024 tiles
 
@@ -1763,9 +1763,10 @@ int tiled_chain(BinScratch &sc, const ItemDesc *items, int n, int shift, int par
   }
   mark(5, s);
   {
-    // 512 threads: three such CTAs (66 KB of shared memory each: the tile
-    // and its fingerprints) fill an SM with 48 warps, enough to hide the
-    // dependent hash and probe latencies
+    // 512 threads: three such CTAs (66 KB of shared memory each, or 50 KB
+    // for a rebuild's split tile, with the fingerprints; registers allow
+    // three) fill an SM with 48 warps, enough to hide the dependent hash and
+    // probe latencies
     constexpr int BA = 512;
     const size_t smem = (fresh ? kSoaTileBytes : (size_t)kTileSlots * sizeof(Slot)) + kFpBytes;
     auto kern = fresh ? k_tile_apply<BA, true, N> : k_tile_apply<BA, false, N>;
