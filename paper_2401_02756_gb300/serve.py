@@ -17,7 +17,7 @@ Stages of one request, each on its own CUDA stream:
    capacity) is reserved against the budget, laid out in memory taken from
    the PyTorch caching allocator (``dbg_create_on``: no cudaMalloc, no
    device synchronisation), and built with every other ready request in one
-   ``dbg_insert_batch`` call: binned chains that take all of the batch's
+   ``dbg_build_batch`` call: binned chains that take all of the batch's
    tables in one launch of each binned kernel, each request's event room
    (its vertex positions, counted on the host) reserved towards the
    library's chain buffers.
@@ -329,7 +329,9 @@ class BuildServer:
             if id(j.ingest_ev) not in seen:
                 s.wait_event(j.ingest_ev)
                 seen.add(id(j.ingest_ev))
-        dbg.insert_batch([(j.graph, j.packed, j.offsets) for j in batch], stream=s)
+        # every table is new: a build (the binned chains' apply then writes each
+        # table tile by tile without reading it)
+        dbg.build_batch([(j.graph, j.packed, j.offsets) for j in batch], stream=s)
         ev = torch.cuda.Event()
         ev.record(s)
         return ev
@@ -354,7 +356,7 @@ class BuildServer:
             j.timing.rebuilds += 1
             self._make_table(j, 2 * j.capacity, s, force=True)
             j.graph.set_tuning(insert_path=1)  # (alone: the direct insert, no chain buffers)
-            j.graph.insert(j.packed, j.offsets, stream=s)
+            j.graph.build(j.packed, j.offsets, stream=s)
         # the sorted export: into device buffers from the allocator (the sort
         # then runs inside them, with 4 bytes a vertex of library scratch),
         # accounted against the budget while they live, then to pinned host
@@ -550,12 +552,12 @@ def sequential(requests: list[Request], predictor: CapacityPredictor, sink=None,
         offsets = torch.from_numpy(r.offsets.view(np.int64)).cuda()
         pred = predictor.predict(r.k, packed, offsets)
         g = dbg.Graph(r.k, predictor.capacity(pred, headroom))
-        g.insert(packed, offsets)
+        g.build(packed, offsets)
         while g.status() != dbg.OK:  # exact fallback, as in the server
             cap = 2 * g.info()["n_slots"]
             g.close()
             g = dbg.Graph(r.k, cap)
-            g.insert(packed, offsets)
+            g.build(packed, offsets)
             t.rebuilds += 1
         s.synchronize()
         t.built = time.perf_counter() - t0
